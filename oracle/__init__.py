@@ -1,0 +1,33 @@
+"""FP64 CPU oracle of the TRINITY time-dependent radiative-transfer forward model.
+
+TEST INFRASTRUCTURE ONLY.  This package is the slow, plain reference that the GPU
+library is checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import it.  The GPU library (package
+``paper_2105_01028_gb300``) never imports, links or calls anything here, and this
+package never imports the library: the two share no code.
+
+Paper: Yajima, Abe, Umemura, Takamizu, Hoshi, "TRINITY: a three-dimensional
+time-dependent radiative transfer code for in-vivo near-infrared imaging"
+(arXiv:2105.01028).  Each function cites the section / equation it follows.
+
+Modules
+-------
+healpix    HEALPix RING pixel centres (§2.1, angular discretisation).
+phase      Henyey-Greenstein phase function (Eq. 11) and the discrete,
+           normalised phase matrix used by the source sum (Eq. 12).
+geometry   Long-ray lattice: dominant axis, sample spacing, per-slab
+           transverse offsets (§2.1, rays independent of the grid; §2.4 Step 1).
+cones      15-degree source / detector acceptance cones (§3.1).
+fresnel    Snell's law (Eq. 13) and Fresnel reflectance (Eq. 14).
+solver     The time loop: ray update (Eqs. 9-10), source iteration (Eq. 12,
+           §2.4 Steps 3, 5, 6, 7), boundary inflow and detectors (§3.1).
+bruteforce An independent per-ray tracer for tiny grids (cross-check of geometry).
+
+Parity status: every function here is pinned by a ``-m "not gpu"`` test in
+``tests/test_oracle_*.py`` except the Fresnel interface redistribution on voxel
+grids (``fresnel.interface_operator``), whose slab-level physics is pinned but whose
+full heterogeneous result is "parity unpinned".
+"""
+
+C0_MM_PER_NS = 299.792458  # speed of light in vacuum, mm/ns (c = c0 / n, §2.1 below Eq. 1)
+RING_DEPTH = 5             # time levels kept per field (retarded upwind needs up to 4 back)
