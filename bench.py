@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Benchmark: cell-direction-step updates/s of the time-dependent RT forward model.
+
+Workload: the phantom-scale homogeneous slab (96 x 96 x 64 voxels at 1 mm, 192 HEALPix
+directions, mu_a 0.008/mm, mu_s 8/mm, g 0.9, n 1.4, 15-degree delta pulse at the centre
+of the -z face, 8 detectors, 10 ps bins).  A bench "step" is one time step of the whole
+path (sweep, source iteration, detector / energy tallies).  The solve is spun up from
+the pulse for --spinup steps (untimed) so that the timed window lies inside the
+developed part of the 1500-step solve; then --warmup steps, then --steps timed steps
+with CUDA events on the library's stream.  The ring history (4.5 GB) is far larger
+than L2, so no L2 flush is needed between steps.
+
+Keys beyond the base contract: "roofline" (the dominant kernel against the measured
+peak), "kernels" (all kernels), "cpu_baseline" (the FP64 oracle timed on the host on a
+bounded voxel sample), "e2e" (the whole job through the public API from host buffers),
+"clocks" (nvidia-smi samples during the timed window), "iterations" (source-iteration
+statistics of the window), "fp32" (the plain-FP32 path on the same window, when the
+headline precision is BF16).
+
+--impl reference times the oracle alone (see cpu_leg) on the same workload.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                  "sm_max_mhz": 2070.0}
+METRIC = "cell*dir*step updates/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            p = json.load(f)
+        p["_source"] = "measured"
+        return p
+    except (OSError, ValueError):
+        p = dict(FALLBACK_PEAKS)
+        p["_source"] = "fallback"
+        return p
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ CPU (oracle) leg
+
+def cpu_leg(prob, n_voxels, seed):
+    """Time the FP64 oracle's work for one time step at ``n_voxels`` random voxels (all
+    directions): the upwind gather, Eq. 10 and the per-voxel source iteration, from a
+    smooth synthetic developed history (the CPU cannot reach the developed part of the
+    solve itself: one full-grid oracle step takes about 30 s).  Returns (updates/s, info)."""
+    from oracle.solver import Model, one_step_at
+    model = Model(dict(prob, tol=prob.get("tol", 1e-6)))
+    Ih, Sh = W.developed_history(prob, seed=seed)
+    levels = Ih.shape[0]
+
+    def hist(which, lev, d, u):
+        arr = Ih if which == "I" else Sh
+        out = np.zeros(np.shape(lev))
+        ok = (lev < 0) & (lev >= -levels)
+        out[ok] = arr[levels + lev[ok], d[ok], u[ok]]
+        return out
+
+    rng = np.random.default_rng(seed)
+    vox = np.sort(rng.choice(model.nv, n_voxels, replace=False))
+    s_glob = float(np.abs(Sh[-1]).max())
+    t0 = time.perf_counter()
+    _, _, iters = one_step_at(model, 0, hist, vox, s_glob)
+    dt = time.perf_counter() - t0
+    return n_voxels * model.na / dt, dict(seconds=dt, voxels=int(n_voxels),
+                                          iters_mean=float(np.mean(iters)))
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    prob = W.config_slab(steps=args.spinup + args.warmup + args.steps)
+    vals = []
+    info = None
+    for k in range(args.warmup + args.steps):
+        v, info = cpu_leg(prob, args.ref_voxels, seed=100 + k)
+        if k >= args.warmup:
+            vals.append(v)
+    value = float(np.mean(vals))
+    sample = ("per bench step: one time step of the FP64 oracle at %d random voxels x 192 "
+              "directions of the 96x96x64 slab (sweep gather, Eq. 10, source iteration to "
+              "tol 1e-6) from a synthetic developed history" % args.ref_voxels)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "updates/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * info["seconds"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args),
+            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": cpu_cores(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ GPU leg
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is None:
+            self.out = ""
+            return
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                try:
+                    rows.append((float(parts[0]), float(parts[1]), parts[3:7]))
+                except ValueError:
+                    pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, x in enumerate(r) if x.lower() == "active"})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def workload_config(args):
+    return {"workload": "phantom-scale slab 96x96x64 voxels @1mm, 192 HEALPix dirs (Nside 4), "
+                        "mu_a 0.008/mm, mu_s 8/mm, g 0.9, n 1.4, 15-deg delta pulse, 8 detectors, "
+                        "10 ps bins",
+            "window": "time steps %d..%d of the 1500-step solve" % (
+                args.spinup + args.warmup, args.spinup + args.warmup + args.steps - 1),
+            "tol": 1e-6, "l2": "inputs larger than L2 (4.5 GB time-level history per solve)",
+            "parallelism": "replicas" if dist_env()[0] > 1 else "single GPU"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--spinup", type=int, default=600)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--compare-fp32", action="store_true",
+                    help="also time the plain FP32 path on the same window")
+    ap.add_argument("--cpu-voxels", type=int, default=16384,
+                    help="voxels in the CPU-baseline sample of this arm (about 10 s of oracle work)")
+    ap.add_argument("--ref-voxels", type=int, default=2048,
+                    help="voxels per bench step of --impl reference")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import paper_2105_01028_gb300 as T
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    total = args.spinup + args.warmup + args.steps + 16
+    prob = W.config_slab(steps=total, precision=args.precision)
+    stream = torch.cuda.Stream()
+    nv = prob["nx"] * prob["ny"] * prob["nz"]
+    na = 12 * prob["nside"] ** 2
+
+    # ---- e2e job through the public API, from host buffers: optics upload, spin-up,
+    # warm-up and the timed window, per-step tallies and detector curves read back.
+    t_job0 = time.perf_counter()
+    fwd = T.Forward(prob, stream=stream.cuda_stream)
+    fwd.run(args.spinup)
+    fwd.run(args.warmup)
+    fwd.sync()
+    first = fwd.steps_done()
+
+    # ---- timed window (device time, CUDA events on the library's stream)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        fwd.run(args.steps)
+        ev1.record(stream)
+        stream.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    torch.cuda.synchronize()
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    status = fwd.sync()
+    det = fwd.detectors()
+    N, esc = fwd.energy()
+    t_job = time.perf_counter() - t_job0
+    job_steps = fwd.steps_done()
+    it_max, it_mean = fwd.iterations()
+    win_max = it_max[first:first + args.steps]
+    win_mean = it_mean[first:first + args.steps]
+
+    # ---- per-kernel device times (CUDA events around each kernel, right after the window)
+    kp = min(args.steps, 10)
+    kms = fwd.profile(kp)
+    k_it_max, k_it_mean = fwd.iterations()
+    k_mean = float(np.mean(k_it_mean[-kp:]))
+    fwd.close()
+
+    updates = nv * na * args.steps
+    value = ws * updates / (ms * 1e-3)
+    pk = peaks()
+    hbm = pk["hbm_gbs"]
+    sweep_bytes = nv * na * 20 + nv * 8  # I,S at two levels read (16 B), Q written (4 B); optics
+    scat_bytes = nv * na * 16 + nv * 12  # Q, S(n-1) read, I, S written; optics
+    scat_flops = 2.0 * na * na * nv * k_mean  # angular sum per voxel per iteration
+    per = [kms[0] / kp, kms[1] / kp, kms[2] / kp]
+    tot = sum(per)
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    if args.precision == "bf16":
+        s_bound, s_peak, s_unit = "tensor", pk.get("bf16_tflops_sustained", 1700.0), "TFLOP/s"
+    else:
+        s_bound, s_peak, s_unit = "alu", fp32_peak, "TFLOP/s"
+    s_ach = scat_flops / (per[1] * 1e-3) / 1e12
+    w_ach = sweep_bytes / (per[0] * 1e-3) / 1e9
+    kernels = [
+        {"name": "sweep", "ms": per[0], "share": per[0] / tot, "bound": "hbm",
+         "achieved": w_ach, "peak": hbm, "unit": "GB/s", "frac": w_ach / hbm,
+         "algorithmic_bytes": sweep_bytes},
+        {"name": "scatter_" + args.precision, "ms": per[1], "share": per[1] / tot,
+         "bound": s_bound, "achieved": s_ach, "peak": s_peak, "unit": s_unit,
+         "frac": s_ach / s_peak, "algorithmic_flops": scat_flops,
+         "hbm_gbs": scat_bytes / (per[1] * 1e-3) / 1e9},
+        {"name": "tally+advance", "ms": per[2], "share": per[2] / tot},
+    ]
+    dom = max(kernels[:2], key=lambda k: k["ms"])
+    roof = {"kernel": dom["name"], "bound": dom["bound"], "achieved": dom["achieved"],
+            "peak": dom["peak"], "unit": dom["unit"], "frac": dom["frac"], "traffic": None,
+            "peak_source": pk["_source"] + (" (FP32 FFMA: 152 SMs x 128 lanes x 2 x max SM clock)"
+                                            if dom["bound"] == "alu" else "")}
+
+    line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16-scatter/f32-sweep" if args.precision == "bf16" else "f32",
+            "data": "synthetic", "config": workload_config(args),
+            "gpu_launches": 4 * args.steps,
+            "iterations": {"mean": float(np.mean(win_mean)), "max": int(np.max(win_max))},
+            "status": int(status),
+            "roofline": roof, "kernels": kernels, "clocks": clk.summary(),
+            "e2e": {"value": ws * nv * na * job_steps / t_job, "unit": "updates/s",
+                    "what": "whole job from host buffers: context + optics upload, %d steps, "
+                            "tallies and detector curves read back" % job_steps,
+                    "h2d_bytes_per_step": 3 * nv * 4 / job_steps,
+                    "d2h_bytes_per_step": (det.size * 8 + N.size * 16) / job_steps}}
+
+    if args.compare_fp32 and args.precision != "fp32":
+        p32 = W.config_slab(steps=total, precision="fp32")
+        f32 = T.Forward(p32, stream=stream.cuda_stream)
+        f32.run(args.spinup + args.warmup)
+        f32.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f32.run(args.steps)
+        e1.record(stream)
+        stream.synchronize()
+        m32 = e0.elapsed_time(e1)
+        line["fp32"] = {"value": ws * updates / (m32 * 1e-3), "ms_per_step": m32 / args.steps}
+        f32.close()
+
+    if rank == 0 and not args.no_cpu and ws >= 1:
+        v, info = cpu_leg(prob, args.cpu_voxels, seed=100)
+        line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": cpu_cores(),
+                                "kind": "oracle",
+                                "sample": "one time step of the FP64 oracle at %d random voxels x 192 "
+                                          "directions from a synthetic developed history (%.1f s, "
+                                          "%.0f iterations/voxel mean)" % (
+                                              info["voxels"], info["seconds"], info["iters_mean"])}
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/*
+ * trinity.h -- C ABI of the GB300 time-dependent radiative-transfer forward model.
+ *
+ * The library solves the time-dependent radiative transfer equation (Eq. 1 of
+ * Yajima et al., "TRINITY: a three-dimensional time-dependent radiative transfer code
+ * for in-vivo near-infrared imaging", arXiv:2105.01028) on a uniform voxel grid with
+ * HEALPix directions, with the paper's retarded long-characteristic update (Eqs. 9-10)
+ * and per-step source iteration (Eq. 12, Section 2.4 steps 3, 5, 6, 7), and bins the
+ * escaping light into time-resolved detector curves (Section 3.1).
+ *
+ * Conventions for every entry point:
+ *   - Units: mm, 1/mm, ns.  Voxel arrays are [nz][ny][nx] (x fastest), float32.
+ *   - Directions are HEALPix RING order, N_a = 12 * nside^2.  Device fields are laid out
+ *     [direction][voxel].
+ *   - Faces are 0..5 = -x, +x, -y, +y, -z, +z.  A point on a face is (u, v) in mm along
+ *     the face's two other axes in increasing order (x face: (y, z); y face: (x, z);
+ *     z face: (x, y)).
+ *   - Inputs are copied; the caller keeps ownership of every pointer it passes.  Output
+ *     buffers are allocated by the caller.  ``ptr_kind`` 0 = host pointer, 1 = device
+ *     pointer (device memory of the context's GPU).
+ *   - Every call returns a trinity_status; on error the context keeps a message readable
+ *     with trinity_last_error().  Nothing aborts the process and no exception crosses
+ *     the ABI.  Calls on one context are not thread-safe; separate contexts are
+ *     independent.
+ *   - All device work of a context is issued on the stream given at creation (0 = the
+ *     legacy default stream); calls that return data to the host synchronise that stream.
+ *   - Device-side waits inside kernels are bounded; a wait that runs out sets an error
+ *     word that the next call reports as TRINITY_E_TIMEOUT.
+ */
+#ifndef TRINITY_H
+#define TRINITY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct trinity_ctx trinity_ctx;
+
+typedef enum {
+  TRINITY_OK = 0,
+  TRINITY_W_NOT_CONVERGED = 1, /* completed, but some voxel hit max_iters in a step */
+  TRINITY_E_INVALID = -1,      /* bad argument or unsupported combination */
+  TRINITY_E_OOM = -2,          /* device allocation failed */
+  TRINITY_E_CUDA = -3,         /* a CUDA call failed (message has the CUDA error) */
+  TRINITY_E_STATE = -4,        /* call not allowed in the context's current state */
+  TRINITY_E_TIMEOUT = -5,      /* a bounded device-side wait ran out */
+  TRINITY_E_UNSUPPORTED = -6   /* the device cannot run this (e.g. not sm_103) */
+} trinity_status;
+
+enum { TRINITY_BOUNDARY_VACUUM = 0, TRINITY_BOUNDARY_PERIODIC = 1 };
+enum { TRINITY_FP32 = 0, TRINITY_BF16 = 1 };
+enum { TRINITY_FIELD_I = 0, TRINITY_FIELD_S = 1 };
+
+/*
+ * Grid and solver description.
+ *   nx, ny, nz   voxels per axis (>= 2 each); h_mm voxel size.
+ *   nside        HEALPix resolution: 1, 2 or 4 (12, 48, 192 directions).
+ *   courant      c0 * dt / (n_ref * h): the time step dt = courant * h * n_ref / c0
+ *                (the paper's rule "dt = fraction x light-crossing time of a grid",
+ *                Sections 2.2 and 3.1).
+ *   n_ref        refractive index used to define dt.
+ *   boundary     TRINITY_BOUNDARY_VACUUM (absorbing faces, Section 3.1) or _PERIODIC.
+ *   precision    TRINITY_FP32 (all arithmetic FP32) or TRINITY_BF16 (the angular
+ *                scattering sum of Eq. 12 in BF16 with FP32 accumulation on the tensor
+ *                cores; transport FP32; detector and energy sums FP64 in both modes).
+ *   tol          source-iteration tolerance (relative, see trinity_step).
+ *   max_iters    source-iteration cap per step (>= 1).
+ */
+typedef struct {
+  int nx, ny, nz;
+  double h_mm;
+  int nside;
+  double courant;
+  double n_ref;
+  int boundary;
+  int precision;
+  double tol;
+  int max_iters;
+} trinity_grid_desc;
+
+/* Bytes of device memory a context with this description allocates (for admission
+ * control).  Returns 0 for an invalid description. */
+size_t trinity_footprint_bytes(const trinity_grid_desc* desc);
+
+/* Create a context: checks the device (sm_103), builds the direction table, the ray
+ * lattice (Section 2.1, rays independent of the grid; Section 2.4 step 1) and allocates
+ * the time-level history of I and S (the paper keeps several time bins of I and S,
+ * Section 2.2).  ``cuda_stream`` is a cudaStream_t or NULL.  *out is NULL on error. */
+int trinity_create_grid(const trinity_grid_desc* desc, void* cuda_stream, trinity_ctx** out);
+
+/* Optical maps (Eq. 1): mu_a, mu_s (1/mm, >= 0) and refractive index n (>= 1) per voxel,
+ * [nz][ny][nx] float32, host (ptr_kind 0) or device (1) pointers; g is the global
+ * Henyey-Greenstein anisotropy (Eq. 11), -1 < g < 1.  Every voxel's retarded delay
+ * ds * n / (c0 dt) must lie in [1, 4) steps, else TRINITY_E_INVALID.  Must be called
+ * before the first step; calling it again resets the run. */
+int trinity_set_optics(trinity_ctx* ctx, const float* mua, const float* mus, const float* n,
+                       double g, int ptr_kind);
+int trinity_set_optics_uniform(trinity_ctx* ctx, double mua, double mus, double g, double n);
+
+/* Collimated pulse (Section 3.1): enters through the face voxel containing (u_mm, v_mm)
+ * of ``face``, within a cone of ``half_angle_deg`` around the inward normal, during the
+ * first ``pulse_steps`` time levels, carrying ``energy`` in total.  The cone's solid
+ * angle is shared among directions by nearest pixel centre.  Only vacuum boundaries. */
+int trinity_set_source(trinity_ctx* ctx, int face, double u_mm, double v_mm,
+                       double half_angle_deg, int pulse_steps, double energy);
+
+/* A surface detector (Section 3.1): the face voxels whose centres lie within radius_mm
+ * of (u_mm, v_mm) collect the outgoing flux inside a cone of half_angle_deg around the
+ * outward normal.  *det_id receives its index (0, 1, ...).  Before the first step. */
+int trinity_add_detector(trinity_ctx* ctx, int face, double u_mm, double v_mm,
+                         double radius_mm, double half_angle_deg, int* det_id);
+
+/* Detector time bins: step n (covering [n dt, (n+1) dt)) goes to bin
+ * floor((n + 1/2) dt / bin_ps); steps past nbins are not binned.  Before the first step. */
+int trinity_set_bins(trinity_ctx* ctx, double bin_ps, int nbins);
+
+/* The field at every time level before 0 (default: zero).  I0, S0 are [N_a][nz*ny*nx]
+ * float32.  Before the first step. */
+int trinity_set_initial_state(trinity_ctx* ctx, const float* I0, const float* S0, int ptr_kind);
+
+/* Advance ``nsteps`` time steps.  Each step: the ray sweep (Eq. 10 with retarded upwind
+ * I and S, linear in time between stored levels), the per-voxel source iteration
+ * S = a P (Q + b1 S) of Eq. 12 started from S(n-1) and stopped when
+ *   rho/(1-rho) |S^k - S^(k-1)|_inf <= tol * max(|S^k|_inf, 1e-6 * max|S(n-1)|)
+ * (rho = a * max_d b1, a bound on the contraction) or when the change falls to the
+ * arithmetic's own resolution, then the detector and energy tallies.  iters_out (may be
+ * NULL) receives the largest iteration count of each step.  Returns
+ * TRINITY_W_NOT_CONVERGED if any voxel hit max_iters. */
+int trinity_step(trinity_ctx* ctx, int nsteps, int* iters_out);
+
+/* Same as trinity_step without per-step read-back: the steps are replayed from a
+ * captured CUDA graph and the call returns once they are queued (no host sync). */
+int trinity_run(trinity_ctx* ctx, int nsteps);
+
+/* Advance ``nsteps`` steps with CUDA events around each kernel (on the context's stream)
+ * and return the summed device time in ms of the sweep, the source iteration and the
+ * tallies (tally + step counter): kernel_ms[3].  Synchronous; for measurement. */
+int trinity_profile_steps(trinity_ctx* ctx, int nsteps, double* kernel_ms);
+
+/* Block until queued work is done; reports errors of earlier asynchronous calls. */
+int trinity_sync(trinity_ctx* ctx);
+
+/* Detector curves, FP64 [n_det][nbins] (n must equal n_det * nbins). */
+int trinity_read_detectors(trinity_ctx* ctx, double* out, size_t n);
+
+/* Per-step tallies of the last ``nsteps`` completed steps (FP64): photon energy in the box
+ * N(t) = sum_v h^3 n_v / c0 sum_d w I, and energy escaped through all faces in the step.
+ * Either pointer may be NULL. */
+int trinity_read_energy(trinity_ctx* ctx, double* N_t, double* escaped, size_t nsteps);
+
+/* Per-step iteration statistics of the last ``nsteps`` steps: max and mean per voxel. */
+int trinity_read_iterations(trinity_ctx* ctx, int* iters_max, double* iters_mean, size_t nsteps);
+
+/* Copy a field (TRINITY_FIELD_I or _S) at time level (steps_done - 1 - back),
+ * 0 <= back <= 4, into ``out`` ([N_a][nz*ny*nx] float32, ``bytes`` = its size). */
+int trinity_read_field(trinity_ctx* ctx, int what, int back, void* out, size_t bytes, int ptr_kind);
+
+/* Steps completed so far. */
+int trinity_steps_done(const trinity_ctx* ctx, int* n);
+
+/* Zero the fields, tallies and step counter; keep grid, optics, source and detectors. */
+int trinity_reset(trinity_ctx* ctx);
+
+const char* trinity_last_error(const trinity_ctx* ctx);
+void trinity_destroy(trinity_ctx* ctx);
+
+/* ---- Host-side tables (no GPU needed): the same FP64 tables the context builds. ---- */
+
+/* HEALPix RING pixel centres as unit vectors, out[N_a][3] (Section 2.1). */
+int trinity_healpix_dirs(int nside, double* out, size_t n);
+
+/* The normalised discrete phase matrix of Eq. 12, out[N_a][N_a] (row i = outgoing
+ * direction): P = D K D with K_ij = w * HG(Omega_i . Omega_j; g_eff) (Eq. 11), unit row
+ * and column sums, and mean cosine g.  *g_eff (may be NULL) receives g_eff. */
+int trinity_phase_matrix(int nside, double g, double* out, size_t n, double* g_eff);
+
+/* Ray-lattice tables of one grid: per direction dom axis and sign (int32 [N_a][2]),
+ * sample spacing ds (double [N_a]) and per-slab transverse offsets
+ * (int8 [N_a][2][max(nx,ny,nz)]). */
+int trinity_lattice_tables(int nside, int nx, int ny, int nz, double h_mm, int periodic,
+                           int32_t* dom_sgn, double* ds, int8_t* offsets, size_t n_offsets);
+
+/* Cone weights alpha_d (double [N_a]) of a face: the fraction of a cap of half_angle_deg
+ * around the inward (inward = 1) or outward normal nearest to each direction. */
+int trinity_cone_weights(int nside, int face, double half_angle_deg, int inward, double* out,
+                         size_t n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TRINITY_H */

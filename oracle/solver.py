@@ -346,28 +346,22 @@ class Solver:
         return arr[lev % RING_DEPTH].copy()
 
 
-def one_step_at(prob, n, hist, voxels, s_glob):
+def one_step_at(model, n, hist, voxels, s_glob):
     """I(n), S(n) at the given voxels from supplied history (a local, one-step check).
 
-    ``hist(which, levels, dirs, voxels)`` returns the stored field values (levels >= 0 are
-    stored ones; negative levels must return zero).  Used to check a large run sample by
-    sample: everything at level n of the sampled voxels depends only on levels < n and
-    on S(n) of the same voxel.  ``s_glob`` is max |S(n-1)| over the whole grid.
+    ``model`` is a ``Model`` of the problem.  ``hist(which, levels, dirs, voxels)`` returns
+    stored field values (levels >= 0 are stored ones; negative levels must return zero
+    unless the problem has an initial state).  Everything at level n of a voxel depends
+    only on levels < n and on S(n) of the same voxel, so a large run can be checked, or
+    the oracle's per-voxel work timed, sample by sample.  ``s_glob`` is max |S(n-1)| over
+    the whole grid.
     """
-    model = Model(prob)
     seg = model.segment_data(voxels)
-
-    def h(which, lev, d, u):
-        return np.where(lev >= 0, hist(which, lev, d, u), 0.0)
-
-    I_up = _retarded(h, seg, n, "I", model)
-    S_up = _retarded(h, seg, n, "S", model)
+    I_up = _retarded(hist, seg, n, "I", model)
+    S_up = _retarded(hist, seg, n, "S", model)
     Q = I_up * seg["T"] + S_up * seg["b0"]
     vox = seg["vox"]
-    if n > 0:
-        lev = np.full(vox.shape, n - 1)
-        S_prev = np.stack([hist("S", lev, np.full(vox.shape, d), vox) for d in range(model.na)])
-    else:
-        S_prev = np.zeros((model.na, vox.size))
+    lev = np.full(vox.shape, n - 1)
+    S_prev = np.stack([hist("S", lev, np.full(vox.shape, d), vox) for d in range(model.na)])
     S, iters = source_iteration(model, Q, seg["b1"], S_prev, model.albedo[vox], s_glob)
     return Q + seg["b1"] * S, S, iters

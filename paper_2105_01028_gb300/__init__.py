@@ -1,0 +1,227 @@
+"""GB300-native forward model of time-dependent radiative transfer (TRINITY, arXiv:2105.01028).
+
+The compute runs in ``libtrinity.so`` (hand-written sm_103a CUDA behind a C ABI, see
+include/trinity.h).  This package is the thin Python side: ``Forward`` marshals a
+problem description into the C calls and reads results back.  PyTorch is optional and
+only used to pass device buffers and the current CUDA stream.
+"""
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import GridDesc, TrinityError, OK, W_NOT_CONVERGED
+
+FP32, BF16 = 0, 1
+FIELD_I, FIELD_S = 0, 1
+_PREC = {"fp32": FP32, "bf16": BF16}
+_BOUND = {"vacuum": 0, "periodic": 1}
+
+__all__ = ["Forward", "TrinityError", "grid_desc", "footprint_bytes", "healpix_dirs",
+           "phase_matrix", "lattice_tables", "cone_weights", "lib"]
+
+
+def lib():
+    return _lib.load()
+
+
+def grid_desc(prob):
+    """trinity_grid_desc of a problem dict (sizes, angles, time step, precision, tolerance)."""
+    return GridDesc(int(prob["nx"]), int(prob["ny"]), int(prob["nz"]), float(prob["h"]),
+                    int(prob["nside"]), float(prob["courant"]), float(prob["n_ref"]),
+                    _BOUND[prob.get("boundary", "vacuum")], _PREC[prob.get("precision", "fp32")],
+                    float(prob.get("tol", 1e-6)), int(prob.get("max_iters", 2000)))
+
+
+def footprint_bytes(prob):
+    d = grid_desc(prob)
+    return int(lib().trinity_footprint_bytes(ctypes.byref(d)))
+
+
+def _ptr(a):
+    """(pointer, ptr_kind, keep-alive) of a numpy array (host) or a torch CUDA tensor."""
+    if hasattr(a, "data_ptr") and getattr(a, "is_cuda", False):
+        if not a.is_contiguous():
+            raise ValueError("device tensors must be contiguous")
+        return ctypes.c_void_p(a.data_ptr()), 1, a
+    arr = np.ascontiguousarray(a, dtype=np.float32)
+    return arr.ctypes.data_as(ctypes.c_void_p), 0, arr
+
+
+class Forward:
+    """One forward-model context on the current CUDA device.
+
+    ``prob`` is a problem dict (see the ``workloads`` module for the keys).  ``stream`` is
+    a raw cudaStream_t handle (int) or None for the default stream.
+    """
+
+    def __init__(self, prob, stream=None):
+        self.L = lib()
+        self.prob = prob
+        desc = grid_desc(prob)
+        h = ctypes.c_void_p()
+        st = ctypes.c_void_p(stream) if stream else None
+        rc = self.L.trinity_create_grid(ctypes.byref(desc), st, ctypes.byref(h))
+        if rc != OK:
+            raise TrinityError(rc, "trinity_create_grid failed")
+        self.h = h
+        self.nv = desc.nx * desc.ny * desc.nz
+        self.na = 12 * desc.nside * desc.nside
+        self._check(self.set_optics(prob["mua"], prob["mus"], prob["nidx"], prob["g"]))
+        src = prob.get("source")
+        if src is not None:
+            self._check(self.L.trinity_set_source(self.h, int(src["face"]), float(src["u_mm"]),
+                                                  float(src["v_mm"]), float(src["half_angle_deg"]),
+                                                  int(src["pulse_steps"]), float(src["energy"])))
+        self.n_det = 0
+        for det in prob.get("detectors", []):
+            did = ctypes.c_int()
+            self._check(self.L.trinity_add_detector(self.h, int(det["face"]), float(det["u_mm"]),
+                                                    float(det["v_mm"]), float(det["radius_mm"]),
+                                                    float(det["half_angle_deg"]), ctypes.byref(did)))
+            self.n_det += 1
+        self.nbins = int(prob.get("nbins", 1))
+        self._check(self.L.trinity_set_bins(self.h, float(prob.get("bin_ps", 10.0)), self.nbins))
+
+    # -- plumbing
+    def _check(self, rc):
+        if rc not in (OK, W_NOT_CONVERGED):
+            raise TrinityError(rc, self.L.trinity_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.trinity_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- inputs
+    def set_optics(self, mua, mus, nidx, g):
+        pa, ka, keep_a = _ptr(mua)
+        ps, ks, keep_s = _ptr(mus)
+        pn, kn, keep_n = _ptr(nidx)
+        if not (ka == ks == kn):
+            raise ValueError("optics maps must all be host arrays or all device tensors")
+        return self.L.trinity_set_optics(self.h, pa, ps, pn, float(g), ka)
+
+    def set_initial_state(self, I0, S0):
+        pi, ki, keep_i = _ptr(I0)
+        ps, ks, keep_s = _ptr(S0)
+        return self._check(self.L.trinity_set_initial_state(self.h, pi, ps, ki))
+
+    # -- stepping
+    def step(self, nsteps=1):
+        """Advance and return the per-step max iteration counts (synchronous)."""
+        out = (ctypes.c_int * max(nsteps, 1))()
+        rc = self._check(self.L.trinity_step(self.h, int(nsteps), out))
+        self.last_status = rc
+        return np.array(out[:nsteps], dtype=np.int64)
+
+    def run(self, nsteps):
+        """Queue ``nsteps`` steps (CUDA-graph replay); returns without waiting."""
+        return self._check(self.L.trinity_run(self.h, int(nsteps)))
+
+    def profile(self, nsteps):
+        """Advance ``nsteps`` steps timing each kernel with CUDA events; returns the summed
+        device ms of (sweep, source iteration, tallies)."""
+        ms = np.zeros(3)
+        self._check(self.L.trinity_profile_steps(self.h, int(nsteps), ms.ctypes.data_as(_lib.P_double)))
+        return ms
+
+    def sync(self):
+        self.last_status = self._check(self.L.trinity_sync(self.h))
+        return self.last_status
+
+    def reset(self):
+        return self._check(self.L.trinity_reset(self.h))
+
+    # -- outputs
+    def steps_done(self):
+        n = ctypes.c_int()
+        self._check(self.L.trinity_steps_done(self.h, ctypes.byref(n)))
+        return n.value
+
+    def detectors(self):
+        out = np.zeros((self.n_det, self.nbins))
+        self._check(self.L.trinity_read_detectors(
+            self.h, out.ctypes.data_as(_lib.P_double), out.size))
+        return out
+
+    def energy(self, nsteps=None):
+        nsteps = self.steps_done() if nsteps is None else nsteps
+        N = np.zeros(nsteps)
+        E = np.zeros(nsteps)
+        self._check(self.L.trinity_read_energy(self.h, N.ctypes.data_as(_lib.P_double),
+                                               E.ctypes.data_as(_lib.P_double), nsteps))
+        return N, E
+
+    def iterations(self, nsteps=None):
+        nsteps = self.steps_done() if nsteps is None else nsteps
+        mx = np.zeros(nsteps, dtype=np.int32)
+        mean = np.zeros(nsteps)
+        self._check(self.L.trinity_read_iterations(self.h, mx.ctypes.data_as(_lib.P_int),
+                                                   mean.ctypes.data_as(_lib.P_double), nsteps))
+        return mx, mean
+
+    def field(self, what=FIELD_I, back=0, out=None):
+        """Field at level steps_done-1-back as a host array [N_a, N_v] (or into a CUDA tensor)."""
+        if out is not None and getattr(out, "is_cuda", False):
+            self._check(self.L.trinity_read_field(self.h, what, back, ctypes.c_void_p(out.data_ptr()),
+                                                  out.numel() * 4, 1))
+            return out
+        arr = np.empty((self.na, self.nv), dtype=np.float32)
+        self._check(self.L.trinity_read_field(self.h, what, back, arr.ctypes.data_as(ctypes.c_void_p),
+                                              arr.nbytes, 0))
+        return arr
+
+
+# ---- host tables (no GPU needed)
+
+def healpix_dirs(nside):
+    n = 12 * nside * nside
+    out = np.zeros((n, 3))
+    rc = lib().trinity_healpix_dirs(nside, out.ctypes.data_as(_lib.P_double), out.size)
+    if rc != OK:
+        raise TrinityError(rc, "healpix_dirs")
+    return out
+
+
+def phase_matrix(nside, g):
+    n = 12 * nside * nside
+    out = np.zeros((n, n))
+    geff = ctypes.c_double()
+    rc = lib().trinity_phase_matrix(nside, float(g), out.ctypes.data_as(_lib.P_double), out.size,
+                                    ctypes.byref(geff))
+    if rc != OK:
+        raise TrinityError(rc, "phase_matrix")
+    return out, geff.value
+
+
+def lattice_tables(nside, nx, ny, nz, h=1.0, periodic=False):
+    n = 12 * nside * nside
+    nmax = max(nx, ny, nz)
+    dom_sgn = np.zeros((n, 2), dtype=np.int32)
+    ds = np.zeros(n)
+    offs = np.zeros((n, 2, nmax), dtype=np.int8)
+    rc = lib().trinity_lattice_tables(nside, nx, ny, nz, float(h), int(periodic),
+                                      dom_sgn.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                      ds.ctypes.data_as(_lib.P_double),
+                                      offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), offs.size)
+    if rc != OK:
+        raise TrinityError(rc, "lattice_tables")
+    return dom_sgn, ds, offs
+
+
+def cone_weights(nside, face, half_angle_deg, inward):
+    n = 12 * nside * nside
+    out = np.zeros(n)
+    rc = lib().trinity_cone_weights(nside, face, float(half_angle_deg), int(inward),
+                                    out.ctypes.data_as(_lib.P_double), n)
+    if rc != OK:
+        raise TrinityError(rc, "cone_weights")
+    return out

@@ -1,0 +1,881 @@
+// C ABI of the forward model (declared in include/trinity.h): context lifetime, inputs,
+// the per-step launch sequence, CUDA-graph replay and read-backs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <exception>
+#include <string>
+#include <vector>
+
+#include "device.cuh"
+#include "host_tables.h"
+#include "trinity.h"
+
+using namespace trinity;
+
+namespace trinity {
+cudaError_t launch_scatter_bf16(const GridParams& g, const DirInfo* dirs, const uint16_t* Pbf,
+                                const float* Q, const float* mut, const float* alb,
+                                const float* nidx, float* Iring, float* Sring, float tol,
+                                int max_iters, RunState rs, cudaStream_t st);
+bool scatter_bf16_supported(int na);
+}  // namespace trinity
+
+struct trinity_ctx {
+  trinity_grid_desc desc{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  GridParams g{};
+  double dt = 0.0;
+  double w = 0.0;
+  double g_aniso = 0.0;
+  std::vector<double> dirs;  // [na][3]
+  Lattice lat;
+  std::vector<DirInfo> hdirs;
+  bool optics_set = false;
+  bool locked = false;  // inputs are frozen once the first step has been queued
+  bool has_init = false;
+  std::string err;
+
+  // detectors
+  struct Det {
+    int face;
+    std::vector<int> vox;
+    std::vector<double> weight;  // per direction, alpha * Omega_cap * cos_out
+  };
+  std::vector<Det> dets;
+  double bin_ps = 10.0;
+  int nbins = 0;
+
+  // device buffers
+  float *I = nullptr, *S = nullptr, *Q = nullptr;
+  float *mut = nullptr, *alb = nullptr, *nidx = nullptr;
+  float* P32 = nullptr;
+  uint16_t* Pbf = nullptr;
+  DirInfo* d_dirs = nullptr;
+  int8_t* d_offs = nullptr;
+  int *d_det_vox = nullptr, *d_det_dir = nullptr, *d_det_id = nullptr;
+  float* d_det_w = nullptr;
+  int n_det_entries = 0;
+  double* d_det = nullptr;
+  // run state
+  int* d_step = nullptr;
+  unsigned* d_smax = nullptr;
+  int* d_nonconv = nullptr;
+  int* d_error = nullptr;
+  int* d_iters_max = nullptr;
+  unsigned long long* d_iters_sum = nullptr;
+  double* d_energy = nullptr;
+  double* d_escaped = nullptr;
+  int* d_bins = nullptr;
+  int capacity = 0;
+  int steps_done = 0;  // steps queued so far
+  int nonconv_seen = 0;
+
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
+};
+
+namespace {
+
+int fail(trinity_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? TRINITY_E_OOM : TRINITY_E_CUDA, \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+  } while (0)
+
+bool desc_valid(const trinity_grid_desc* d, std::string* why) {
+  if (!d) {
+    *why = "null description";
+    return false;
+  }
+  if (d->nx < 2 || d->ny < 2 || d->nz < 2) {
+    *why = "every grid axis needs at least 2 voxels";
+    return false;
+  }
+  if (static_cast<long long>(d->nx) * d->ny * d->nz > (1LL << 30)) {
+    *why = "grid too large";
+    return false;
+  }
+  if (d->nx > 127 * 1024 || d->ny > 127 * 1024 || d->nz > 127 * 1024) {
+    *why = "grid axis too long";
+    return false;
+  }
+  if (!(d->h_mm > 0.0) || !(d->courant > 0.0) || !(d->n_ref >= 1.0)) {
+    *why = "h_mm, courant must be > 0 and n_ref >= 1";
+    return false;
+  }
+  if (d->nside != 1 && d->nside != 2 && d->nside != 4) {
+    *why = "nside must be 1, 2 or 4";
+    return false;
+  }
+  if (d->boundary != TRINITY_BOUNDARY_VACUUM && d->boundary != TRINITY_BOUNDARY_PERIODIC) {
+    *why = "unknown boundary";
+    return false;
+  }
+  if (d->precision != TRINITY_FP32 && d->precision != TRINITY_BF16) {
+    *why = "unknown precision";
+    return false;
+  }
+  if (!(d->tol > 0.0) || d->max_iters < 1) {
+    *why = "tol must be > 0 and max_iters >= 1";
+    return false;
+  }
+  return true;
+}
+
+size_t footprint(const trinity_grid_desc* d) {
+  const size_t nv = static_cast<size_t>(d->nx) * d->ny * d->nz;
+  const size_t na = 12u * d->nside * d->nside;
+  size_t b = 0;
+  b += 2 * kRing * na * nv * sizeof(float);  // I, S history
+  b += na * nv * sizeof(float);              // Q
+  b += 3 * nv * sizeof(float);               // optics
+  b += na * na * (sizeof(float) + sizeof(uint16_t));
+  return b;
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T));
+}
+
+RunState run_state(trinity_ctx* c) {
+  RunState rs;
+  rs.step = c->d_step;
+  rs.smax = c->d_smax;
+  rs.iters_max = c->d_iters_max;
+  rs.iters_sum = c->d_iters_sum;
+  rs.energy = c->d_energy;
+  rs.escaped = c->d_escaped;
+  rs.nonconv = c->d_nonconv;
+  rs.bins = c->d_bins;
+  rs.error = c->d_error;
+  return rs;
+}
+
+// Per-step arrays sized for ``need`` steps (regrown by doubling; drops the graph).
+int ensure_capacity(trinity_ctx* ctx, int need) {
+  if (need <= ctx->capacity) return TRINITY_OK;
+  int cap = std::max(256, ctx->capacity);
+  while (cap < need) cap *= 2;
+  int* im = nullptr;
+  unsigned long long* is = nullptr;
+  double *en = nullptr, *es = nullptr;
+  int* bins = nullptr;
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(dalloc(&im, cap));
+  CK(dalloc(&is, cap));
+  CK(dalloc(&en, cap));
+  CK(dalloc(&es, cap));
+  CK(dalloc(&bins, cap));
+  CK(cudaMemset(im, 0, cap * sizeof(int)));
+  CK(cudaMemset(is, 0, cap * sizeof(unsigned long long)));
+  CK(cudaMemset(en, 0, cap * sizeof(double)));
+  CK(cudaMemset(es, 0, cap * sizeof(double)));
+  if (ctx->capacity > 0) {
+    CK(cudaMemcpy(im, ctx->d_iters_max, ctx->capacity * sizeof(int), cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(is, ctx->d_iters_sum, ctx->capacity * sizeof(unsigned long long),
+                  cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(en, ctx->d_energy, ctx->capacity * sizeof(double), cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(es, ctx->d_escaped, ctx->capacity * sizeof(double), cudaMemcpyDeviceToDevice));
+    cudaFree(ctx->d_iters_max);
+    cudaFree(ctx->d_iters_sum);
+    cudaFree(ctx->d_energy);
+    cudaFree(ctx->d_escaped);
+    cudaFree(ctx->d_bins);
+  }
+  // detector bin of every step: floor((n + 1/2) dt / bin), integers snapped (FP64)
+  std::vector<int> hb(cap);
+  const double bw = ctx->bin_ps * 1e-3;
+  for (int n = 0; n < cap; ++n) {
+    const long b = floor_snap((n + 0.5) * ctx->dt / bw);
+    hb[n] = (b >= 0 && b < ctx->nbins) ? static_cast<int>(b) : -1;
+  }
+  CK(cudaMemcpy(bins, hb.data(), cap * sizeof(int), cudaMemcpyHostToDevice));
+  ctx->d_iters_max = im;
+  ctx->d_iters_sum = is;
+  ctx->d_energy = en;
+  ctx->d_escaped = es;
+  ctx->d_bins = bins;
+  ctx->capacity = cap;
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  return TRINITY_OK;
+}
+
+// Freeze the inputs: upload detector entries and bins before the first step.
+int lock_inputs(trinity_ctx* ctx) {
+  if (ctx->locked) return TRINITY_OK;
+  if (!ctx->optics_set) return fail(ctx, TRINITY_E_STATE, "set_optics must come before stepping");
+  std::vector<int> vox, dir, id;
+  std::vector<float> wt;
+  const double h2dt = ctx->desc.h_mm * ctx->desc.h_mm * ctx->dt;
+  for (size_t k = 0; k < ctx->dets.size(); ++k)
+    for (int v : ctx->dets[k].vox)
+      for (int d = 0; d < ctx->g.na; ++d)
+        if (ctx->dets[k].weight[d] != 0.0) {
+          vox.push_back(v);
+          dir.push_back(d);
+          id.push_back(static_cast<int>(k));
+          wt.push_back(static_cast<float>(ctx->dets[k].weight[d] * h2dt));
+        }
+  ctx->n_det_entries = static_cast<int>(vox.size());
+  CK(dalloc(&ctx->d_det_vox, vox.size()));
+  CK(dalloc(&ctx->d_det_dir, dir.size()));
+  CK(dalloc(&ctx->d_det_id, id.size()));
+  CK(dalloc(&ctx->d_det_w, wt.size()));
+  if (!vox.empty()) {
+    CK(cudaMemcpy(ctx->d_det_vox, vox.data(), vox.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_det_dir, dir.data(), dir.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_det_id, id.data(), id.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_det_w, wt.data(), wt.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  const size_t ndet = ctx->dets.size() * static_cast<size_t>(std::max(ctx->nbins, 1));
+  CK(dalloc(&ctx->d_det, ndet));
+  CK(cudaMemset(ctx->d_det, 0, ndet * sizeof(double)));
+  CK(cudaMemcpy(ctx->d_dirs, ctx->hdirs.data(), ctx->hdirs.size() * sizeof(DirInfo),
+                cudaMemcpyHostToDevice));
+  ctx->locked = true;
+  return TRINITY_OK;
+}
+
+// The launches of one time step (all on ctx->stream; the step index lives on the device).
+int enqueue_step(trinity_ctx* ctx) {
+  const RunState rs = run_state(ctx);
+  const GridParams& g = ctx->g;
+  CK(launch_sweep(g, ctx->d_dirs, ctx->d_offs, ctx->I, ctx->S, ctx->mut, ctx->nidx, ctx->Q, rs,
+                  ctx->stream));
+  if (ctx->desc.precision == TRINITY_BF16) {
+    CK(launch_scatter_bf16(g, ctx->d_dirs, ctx->Pbf, ctx->Q, ctx->mut, ctx->alb, ctx->nidx, ctx->I,
+                           ctx->S, static_cast<float>(ctx->desc.tol), ctx->desc.max_iters, rs,
+                           ctx->stream));
+  } else {
+    CK(launch_scatter_fp32(g, ctx->d_dirs, ctx->P32, ctx->Q, ctx->mut, ctx->alb, ctx->nidx, ctx->I,
+                           ctx->S, static_cast<float>(ctx->desc.tol), ctx->desc.max_iters, rs,
+                           ctx->stream));
+  }
+  CK(launch_tally(g, ctx->d_dirs, ctx->I, ctx->d_det_vox, ctx->d_det_dir, ctx->d_det_w,
+                  ctx->d_det_id, ctx->n_det_entries, ctx->d_det, ctx->nbins, rs, ctx->stream));
+  CK(launch_advance(rs, ctx->stream));
+  return TRINITY_OK;
+}
+
+int check_device_error(trinity_ctx* ctx) {
+  int e = 0;
+  CK(cudaMemcpy(&e, ctx->d_error, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e != 0) return fail(ctx, TRINITY_E_TIMEOUT, "a bounded device wait ran out (code " + std::to_string(e) + ")");
+  return TRINITY_OK;
+}
+
+uint16_t to_bf16(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  const uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7fffu + lsb;  // round to nearest even (inputs are finite)
+  return static_cast<uint16_t>(u >> 16);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t trinity_footprint_bytes(const trinity_grid_desc* desc) {
+  std::string why;
+  if (!desc_valid(desc, &why)) return 0;
+  return footprint(desc);
+}
+
+int trinity_create_grid(const trinity_grid_desc* desc, void* cuda_stream, trinity_ctx** out) {
+  if (!out) return TRINITY_E_INVALID;
+  *out = nullptr;
+  std::string why;
+  if (!desc_valid(desc, &why)) return TRINITY_E_INVALID;
+  trinity_ctx* ctx = nullptr;
+  try {
+    ctx = new trinity_ctx();
+  } catch (...) {
+    return TRINITY_E_OOM;
+  }
+  auto bail = [&](int code) {
+    trinity_destroy(ctx);
+    return code;
+  };
+  ctx->desc = *desc;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(TRINITY_E_CUDA);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, ctx->device) != cudaSuccess) return bail(TRINITY_E_CUDA);
+  if (!(prop.major == 10 && prop.minor == 3)) return bail(TRINITY_E_UNSUPPORTED);
+  if (desc->precision == TRINITY_BF16 && !scatter_bf16_supported(12 * desc->nside * desc->nside))
+    return bail(TRINITY_E_UNSUPPORTED);
+
+  GridParams& g = ctx->g;
+  g.nx = desc->nx;
+  g.ny = desc->ny;
+  g.nz = desc->nz;
+  g.nv = desc->nx * desc->ny * desc->nz;
+  g.na = 12 * desc->nside * desc->nside;
+  g.periodic = desc->boundary == TRINITY_BOUNDARY_PERIODIC;
+  g.hist_from = 0;
+  g.src_voxel = -1;
+  g.pulse_steps = 0;
+  g.h = static_cast<float>(desc->h_mm);
+  ctx->dt = desc->courant * desc->h_mm * desc->n_ref / kC0;
+  ctx->w = 4.0 * 3.14159265358979323846 / g.na;
+  g.e_scale = static_cast<float>(desc->h_mm * desc->h_mm * desc->h_mm / kC0 * ctx->w);
+  try {
+    ctx->dirs = healpix_dirs(desc->nside);
+    ctx->lat = build_lattice(ctx->dirs, g.nx, g.ny, g.nz, desc->h_mm, g.periodic != 0);
+  } catch (const std::exception& e) {
+    return bail(TRINITY_E_INVALID);
+  }
+  g.nmax = ctx->lat.nmax;
+  double dsmax = 0.0;
+  ctx->hdirs.resize(g.na);
+  const double h2dt = desc->h_mm * desc->h_mm * ctx->dt;
+  for (int d = 0; d < g.na; ++d) {
+    DirInfo& di = ctx->hdirs[d];
+    std::memset(&di, 0, sizeof(di));
+    di.dom = ctx->lat.dom[d];
+    di.sgn = ctx->lat.sgn[d];
+    int j = 0, ax[2];
+    for (int a = 0; a < 3; ++a)
+      if (a != di.dom) ax[j++] = a;
+    di.a0 = ax[0];
+    di.a1 = ax[1];
+    di.ds = static_cast<float>(ctx->lat.ds[d]);
+    di.dcoef = static_cast<float>(ctx->lat.ds[d] / (kC0 * ctx->dt));
+    dsmax = std::max(dsmax, ctx->lat.ds[d]);
+    for (int f = 0; f < 6; ++f) {
+      const double c = ((f % 2) ? 1.0 : -1.0) * ctx->dirs[3 * d + f / 2];
+      di.wcos_out[f] = c > 0 ? static_cast<float>(ctx->w * c * h2dt) : 0.0f;
+    }
+  }
+  g.ds_max = static_cast<float>(dsmax);
+
+  const size_t nv = g.nv, na = g.na;
+  if (dalloc(&ctx->I, kRing * na * nv) != cudaSuccess || dalloc(&ctx->S, kRing * na * nv) != cudaSuccess ||
+      dalloc(&ctx->Q, na * nv) != cudaSuccess || dalloc(&ctx->mut, nv) != cudaSuccess ||
+      dalloc(&ctx->alb, nv) != cudaSuccess || dalloc(&ctx->nidx, nv) != cudaSuccess ||
+      dalloc(&ctx->P32, na * na) != cudaSuccess || dalloc(&ctx->Pbf, na * na) != cudaSuccess ||
+      dalloc(&ctx->d_dirs, na) != cudaSuccess ||
+      dalloc(&ctx->d_offs, ctx->lat.off.size()) != cudaSuccess || dalloc(&ctx->d_step, 1) != cudaSuccess ||
+      dalloc(&ctx->d_smax, 2) != cudaSuccess || dalloc(&ctx->d_nonconv, 1) != cudaSuccess ||
+      dalloc(&ctx->d_error, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(TRINITY_E_OOM);
+  }
+  if (cudaMemcpy(ctx->d_offs, ctx->lat.off.data(), ctx->lat.off.size(), cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return bail(TRINITY_E_CUDA);
+  if (trinity_reset(ctx) != TRINITY_OK) return bail(TRINITY_E_CUDA);
+  *out = ctx;
+  return TRINITY_OK;
+}
+
+int trinity_set_optics(trinity_ctx* ctx, const float* mua, const float* mus, const float* n, double g,
+                       int ptr_kind) {
+  if (!ctx) return TRINITY_E_INVALID;
+  if (!mua || !mus || !n || (ptr_kind != 0 && ptr_kind != 1))
+    return fail(ctx, TRINITY_E_INVALID, "null optics pointer or bad ptr_kind");
+  if (!(g > -1.0 && g < 1.0)) return fail(ctx, TRINITY_E_INVALID, "g must lie in (-1, 1)");
+  const size_t nv = ctx->g.nv;
+  std::vector<float> a(nv), s(nv), r(nv);
+  if (ptr_kind == 1) {
+    CK(cudaMemcpy(a.data(), mua, nv * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(s.data(), mus, nv * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(r.data(), n, nv * 4, cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(a.data(), mua, nv * 4);
+    std::memcpy(s.data(), mus, nv * 4);
+    std::memcpy(r.data(), n, nv * 4);
+  }
+  double nmin = 1e30, nmax = -1e30, dsmin = 1e30, dsmax = 0.0;
+  for (double ds : ctx->lat.ds) {
+    dsmin = std::min(dsmin, ds);
+    dsmax = std::max(dsmax, ds);
+  }
+  std::vector<float> mt(nv), al(nv);
+  for (size_t v = 0; v < nv; ++v) {
+    if (!(a[v] >= 0.0f) || !(s[v] >= 0.0f) || !std::isfinite(a[v]) || !std::isfinite(s[v]) ||
+        !(r[v] >= 1.0f) || !std::isfinite(r[v]))
+      return fail(ctx, TRINITY_E_INVALID, "optics need mu_a, mu_s >= 0 and n >= 1, finite");
+    nmin = std::min(nmin, double(r[v]));
+    nmax = std::max(nmax, double(r[v]));
+    mt[v] = a[v] + s[v];
+    al[v] = mt[v] > 0.0f ? s[v] / mt[v] : 0.0f;
+  }
+  const double dlo = dsmin * nmin / (kC0 * ctx->dt), dhi = dsmax * nmax / (kC0 * ctx->dt);
+  if (dlo < 1.0 || dhi >= kRing - 1)
+    return fail(ctx, TRINITY_E_INVALID,
+                "retarded delay outside [1, 4) steps: choose courant so that c dt < h |Omega_dom|");
+  std::vector<double> P;
+  try {
+    P = phase_matrix(ctx->desc.nside, g, nullptr);
+  } catch (const std::exception& e) {
+    return fail(ctx, TRINITY_E_INVALID, e.what());
+  }
+  std::vector<float> P32(P.size());
+  std::vector<uint16_t> Pb(P.size());
+  for (size_t k = 0; k < P.size(); ++k) {
+    P32[k] = static_cast<float>(P[k]);
+    Pb[k] = to_bf16(P32[k]);
+  }
+  CK(cudaMemcpy(ctx->mut, mt.data(), nv * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->alb, al.data(), nv * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->nidx, r.data(), nv * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->P32, P32.data(), P32.size() * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->Pbf, Pb.data(), Pb.size() * 2, cudaMemcpyHostToDevice));
+  ctx->g_aniso = g;
+  ctx->optics_set = true;
+  if (ctx->locked) return trinity_reset(ctx);
+  return TRINITY_OK;
+}
+
+int trinity_set_optics_uniform(trinity_ctx* ctx, double mua, double mus, double g, double n) {
+  if (!ctx) return TRINITY_E_INVALID;
+  const size_t nv = ctx->g.nv;
+  std::vector<float> a(nv, float(mua)), s(nv, float(mus)), r(nv, float(n));
+  return trinity_set_optics(ctx, a.data(), s.data(), r.data(), g, 0);
+}
+
+int trinity_set_source(trinity_ctx* ctx, int face, double u_mm, double v_mm, double half_angle_deg,
+                       int pulse_steps, double energy) {
+  if (!ctx) return TRINITY_E_INVALID;
+  if (ctx->locked) return fail(ctx, TRINITY_E_STATE, "source must be set before the first step");
+  if (ctx->g.periodic) return fail(ctx, TRINITY_E_INVALID, "a source needs vacuum boundaries");
+  if (face < 0 || face > 5 || pulse_steps < 1 || !(energy >= 0.0))
+    return fail(ctx, TRINITY_E_INVALID, "bad face, pulse_steps or energy");
+  const int nn[3] = {ctx->g.nx, ctx->g.ny, ctx->g.nz};
+  const int ax = face / 2;
+  const int ua = ax == 0 ? 1 : 0, va = ax == 2 ? 1 : 2;
+  const long iu = static_cast<long>(std::floor(u_mm / ctx->desc.h_mm));
+  const long iv = static_cast<long>(std::floor(v_mm / ctx->desc.h_mm));
+  if (iu < 0 || iu >= nn[ua] || iv < 0 || iv >= nn[va])
+    return fail(ctx, TRINITY_E_INVALID, "source point outside the face");
+  std::vector<double> alpha;
+  try {
+    alpha = cone_weights(ctx->dirs, face, half_angle_deg, true);
+  } catch (const std::exception& e) {
+    return fail(ctx, TRINITY_E_INVALID, e.what());
+  }
+  const double h = ctx->desc.h_mm;
+  const int entry_sgn = (face % 2 == 0) ? 1 : -1;
+  for (int d = 0; d < ctx->g.na; ++d) {
+    ctx->hdirs[d].src_amp = 0.0f;
+    if (alpha[d] == 0.0) continue;
+    const double cos_in = -((face % 2) ? 1.0 : -1.0) * ctx->dirs[3 * d + ax];
+    if (ctx->lat.dom[d] != ax || ctx->lat.sgn[d] != entry_sgn || !(cos_in > 0.0))
+      return fail(ctx, TRINITY_E_INVALID, "source cone reaches a direction that does not enter through the face");
+    const double amp = energy * alpha[d] / (ctx->w * cos_in * h * h * pulse_steps * ctx->dt);
+    ctx->hdirs[d].src_amp = static_cast<float>(amp);
+  }
+  int c[3];
+  c[ax] = (face % 2) ? nn[ax] - 1 : 0;
+  c[ua] = static_cast<int>(iu);
+  c[va] = static_cast<int>(iv);
+  ctx->g.src_voxel = (c[2] * nn[1] + c[1]) * nn[0] + c[0];
+  ctx->g.pulse_steps = pulse_steps;
+  return TRINITY_OK;
+}
+
+int trinity_add_detector(trinity_ctx* ctx, int face, double u_mm, double v_mm, double radius_mm,
+                         double half_angle_deg, int* det_id) {
+  if (!ctx) return TRINITY_E_INVALID;
+  if (ctx->locked) return fail(ctx, TRINITY_E_STATE, "detectors must be added before the first step");
+  if (face < 0 || face > 5 || !(radius_mm > 0.0)) return fail(ctx, TRINITY_E_INVALID, "bad face or radius");
+  trinity_ctx::Det det;
+  det.face = face;
+  try {
+    const std::vector<double> alpha = cone_weights(ctx->dirs, face, half_angle_deg, false);
+    const double cap = 2.0 * 3.14159265358979323846 * (1.0 - std::cos(half_angle_deg * 3.14159265358979323846 / 180.0));
+    const int ax = face / 2;
+    const double sgn = (face % 2) ? 1.0 : -1.0;
+    det.weight.assign(ctx->g.na, 0.0);
+    for (int d = 0; d < ctx->g.na; ++d) {
+      if (alpha[d] == 0.0) continue;
+      const double c = sgn * ctx->dirs[3 * d + ax];
+      if (!(c > 0.0)) return fail(ctx, TRINITY_E_INVALID, "detector cone reaches an incoming direction");
+      det.weight[d] = alpha[d] * cap * c;
+    }
+  } catch (const std::exception& e) {
+    return fail(ctx, TRINITY_E_INVALID, e.what());
+  }
+  const int nn[3] = {ctx->g.nx, ctx->g.ny, ctx->g.nz};
+  const int ax = face / 2;
+  const int ua = ax == 0 ? 1 : 0, va = ax == 2 ? 1 : 2;
+  const double h = ctx->desc.h_mm;
+  for (int iu = 0; iu < nn[ua]; ++iu)
+    for (int iv = 0; iv < nn[va]; ++iv) {
+      const double du = (iu + 0.5) * h - u_mm, dv = (iv + 0.5) * h - v_mm;
+      if (du * du + dv * dv <= radius_mm * radius_mm * (1.0 + 1e-12)) {
+        int c[3];
+        c[ax] = (face % 2) ? nn[ax] - 1 : 0;
+        c[ua] = iu;
+        c[va] = iv;
+        det.vox.push_back((c[2] * nn[1] + c[1]) * nn[0] + c[0]);
+      }
+    }
+  std::sort(det.vox.begin(), det.vox.end());
+  ctx->dets.push_back(det);
+  if (det_id) *det_id = static_cast<int>(ctx->dets.size()) - 1;
+  return TRINITY_OK;
+}
+
+int trinity_set_bins(trinity_ctx* ctx, double bin_ps, int nbins) {
+  if (!ctx) return TRINITY_E_INVALID;
+  if (ctx->locked) return fail(ctx, TRINITY_E_STATE, "bins must be set before the first step");
+  if (!(bin_ps > 0.0) || nbins < 1) return fail(ctx, TRINITY_E_INVALID, "bad bin width or count");
+  ctx->bin_ps = bin_ps;
+  ctx->nbins = nbins;
+  if (ctx->capacity > 0) {  // rebuild the bin table for the new width
+    const int cap = ctx->capacity;
+    ctx->capacity = 0;
+    cudaFree(ctx->d_iters_max);
+    cudaFree(ctx->d_iters_sum);
+    cudaFree(ctx->d_energy);
+    cudaFree(ctx->d_escaped);
+    cudaFree(ctx->d_bins);
+    ctx->d_iters_max = nullptr;
+    ctx->d_iters_sum = nullptr;
+    ctx->d_energy = nullptr;
+    ctx->d_escaped = nullptr;
+    ctx->d_bins = nullptr;
+    return ensure_capacity(ctx, cap);
+  }
+  return TRINITY_OK;
+}
+
+int trinity_set_initial_state(trinity_ctx* ctx, const float* I0, const float* S0, int ptr_kind) {
+  if (!ctx) return TRINITY_E_INVALID;
+  if (ctx->locked || ctx->steps_done > 0) return fail(ctx, TRINITY_E_STATE, "initial state must precede the first step");
+  if (!I0 || !S0 || (ptr_kind != 0 && ptr_kind != 1)) return fail(ctx, TRINITY_E_INVALID, "bad initial state");
+  const size_t cnt = static_cast<size_t>(ctx->g.na) * ctx->g.nv;
+  const cudaMemcpyKind kind = ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  for (int lev = -(kRing - 1); lev < 0; ++lev) {
+    const size_t off = static_cast<size_t>(ring_slot(lev)) * cnt;
+    CK(cudaMemcpy(ctx->I + off, I0, cnt * 4, kind));
+    CK(cudaMemcpy(ctx->S + off, S0, cnt * 4, kind));
+  }
+  std::vector<float> hs(cnt);
+  CK(cudaMemcpy(hs.data(), S0, cnt * 4, ptr_kind ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+  float m = 0.0f;
+  for (float x : hs) m = std::max(m, std::fabs(x));
+  unsigned bits;
+  std::memcpy(&bits, &m, 4);
+  CK(cudaMemcpy(ctx->d_smax + 1, &bits, 4, cudaMemcpyHostToDevice));
+  ctx->g.hist_from = -(kRing - 1);
+  ctx->has_init = true;
+  return TRINITY_OK;
+}
+
+int trinity_step(trinity_ctx* ctx, int nsteps, int* iters_out) {
+  if (!ctx) return TRINITY_E_INVALID;
+  if (nsteps < 0) return fail(ctx, TRINITY_E_INVALID, "nsteps < 0");
+  int rc = lock_inputs(ctx);
+  if (rc != TRINITY_OK) return rc;
+  rc = ensure_capacity(ctx, ctx->steps_done + nsteps);
+  if (rc != TRINITY_OK) return rc;
+  for (int s = 0; s < nsteps; ++s) {
+    rc = enqueue_step(ctx);
+    if (rc != TRINITY_OK) return rc;
+  }
+  const int first = ctx->steps_done;
+  ctx->steps_done += nsteps;
+  CK(cudaStreamSynchronize(ctx->stream));
+  rc = check_device_error(ctx);
+  if (rc != TRINITY_OK) return rc;
+  if (iters_out && nsteps > 0)
+    CK(cudaMemcpy(iters_out, ctx->d_iters_max + first, nsteps * sizeof(int), cudaMemcpyDeviceToHost));
+  int nc = 0;
+  CK(cudaMemcpy(&nc, ctx->d_nonconv, sizeof(int), cudaMemcpyDeviceToHost));
+  if (nc > ctx->nonconv_seen) {
+    ctx->nonconv_seen = nc;
+    ctx->err = "some voxels reached max_iters";
+    return TRINITY_W_NOT_CONVERGED;
+  }
+  return TRINITY_OK;
+}
+
+int trinity_run(trinity_ctx* ctx, int nsteps) {
+  if (!ctx) return TRINITY_E_INVALID;
+  if (nsteps < 0) return fail(ctx, TRINITY_E_INVALID, "nsteps < 0");
+  int rc = lock_inputs(ctx);
+  if (rc != TRINITY_OK) return rc;
+  rc = ensure_capacity(ctx, ctx->steps_done + nsteps);
+  if (rc != TRINITY_OK) return rc;
+  constexpr int kGraphSteps = 8;
+  if (!ctx->graph) {
+    cudaStream_t cap_stream;
+    CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+    cudaStream_t saved = ctx->stream;
+    ctx->stream = cap_stream;
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
+    int erc = TRINITY_OK;
+    for (int s = 0; s < kGraphSteps && erc == TRINITY_OK; ++s) erc = enqueue_step(ctx);
+    cudaError_t ce = cudaStreamEndCapture(cap_stream, &graph);
+    ctx->stream = saved;
+    cudaStreamDestroy(cap_stream);
+    if (erc != TRINITY_OK) return erc;
+    CK(ce);
+    ce = cudaGraphInstantiate(&ctx->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ce);
+    ctx->graph_steps = kGraphSteps;
+  }
+  int left = nsteps;
+  while (left >= ctx->graph_steps) {
+    CK(cudaGraphLaunch(ctx->graph, ctx->stream));
+    left -= ctx->graph_steps;
+  }
+  for (int s = 0; s < left; ++s) {
+    rc = enqueue_step(ctx);
+    if (rc != TRINITY_OK) return rc;
+  }
+  ctx->steps_done += nsteps;
+  return TRINITY_OK;
+}
+
+int trinity_profile_steps(trinity_ctx* ctx, int nsteps, double* kernel_ms) {
+  if (!ctx || !kernel_ms) return TRINITY_E_INVALID;
+  if (nsteps < 1) return fail(ctx, TRINITY_E_INVALID, "nsteps < 1");
+  int rc = lock_inputs(ctx);
+  if (rc != TRINITY_OK) return rc;
+  rc = ensure_capacity(ctx, ctx->steps_done + nsteps);
+  if (rc != TRINITY_OK) return rc;
+  const RunState rs = run_state(ctx);
+  const GridParams& g = ctx->g;
+  std::vector<cudaEvent_t> ev(4 * static_cast<size_t>(nsteps));
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  for (int s = 0; s < nsteps; ++s) {
+    cudaEvent_t* e = &ev[4 * static_cast<size_t>(s)];
+    CK(cudaEventRecord(e[0], ctx->stream));
+    CK(launch_sweep(g, ctx->d_dirs, ctx->d_offs, ctx->I, ctx->S, ctx->mut, ctx->nidx, ctx->Q, rs,
+                    ctx->stream));
+    CK(cudaEventRecord(e[1], ctx->stream));
+    if (ctx->desc.precision == TRINITY_BF16)
+      CK(launch_scatter_bf16(g, ctx->d_dirs, ctx->Pbf, ctx->Q, ctx->mut, ctx->alb, ctx->nidx, ctx->I,
+                             ctx->S, static_cast<float>(ctx->desc.tol), ctx->desc.max_iters, rs,
+                             ctx->stream));
+    else
+      CK(launch_scatter_fp32(g, ctx->d_dirs, ctx->P32, ctx->Q, ctx->mut, ctx->alb, ctx->nidx, ctx->I,
+                             ctx->S, static_cast<float>(ctx->desc.tol), ctx->desc.max_iters, rs,
+                             ctx->stream));
+    CK(cudaEventRecord(e[2], ctx->stream));
+    CK(launch_tally(g, ctx->d_dirs, ctx->I, ctx->d_det_vox, ctx->d_det_dir, ctx->d_det_w,
+                    ctx->d_det_id, ctx->n_det_entries, ctx->d_det, ctx->nbins, rs, ctx->stream));
+    CK(launch_advance(rs, ctx->stream));
+    CK(cudaEventRecord(e[3], ctx->stream));
+  }
+  ctx->steps_done += nsteps;
+  CK(cudaStreamSynchronize(ctx->stream));
+  kernel_ms[0] = kernel_ms[1] = kernel_ms[2] = 0.0;
+  for (int s = 0; s < nsteps; ++s) {
+    for (int k = 0; k < 3; ++k) {
+      float ms = 0.0f;
+      CK(cudaEventElapsedTime(&ms, ev[4 * static_cast<size_t>(s) + k], ev[4 * static_cast<size_t>(s) + k + 1]));
+      kernel_ms[k] += ms;
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  return check_device_error(ctx);
+}
+
+int trinity_sync(trinity_ctx* ctx) {
+  if (!ctx) return TRINITY_E_INVALID;
+  CK(cudaStreamSynchronize(ctx->stream));
+  int rc = check_device_error(ctx);
+  if (rc != TRINITY_OK) return rc;
+  int nc = 0;
+  CK(cudaMemcpy(&nc, ctx->d_nonconv, sizeof(int), cudaMemcpyDeviceToHost));
+  if (nc > ctx->nonconv_seen) {
+    ctx->nonconv_seen = nc;
+    ctx->err = "some voxels reached max_iters";
+    return TRINITY_W_NOT_CONVERGED;
+  }
+  return TRINITY_OK;
+}
+
+int trinity_read_detectors(trinity_ctx* ctx, double* out, size_t n) {
+  if (!ctx) return TRINITY_E_INVALID;
+  const size_t want = ctx->dets.size() * static_cast<size_t>(ctx->nbins);
+  if (n != want || (want > 0 && !out)) return fail(ctx, TRINITY_E_INVALID, "detector buffer size mismatch");
+  if (want == 0) return TRINITY_OK;
+  if (!ctx->locked) {
+    std::fill(out, out + n, 0.0);
+    return TRINITY_OK;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy(out, ctx->d_det, want * sizeof(double), cudaMemcpyDeviceToHost));
+  return TRINITY_OK;
+}
+
+int trinity_read_energy(trinity_ctx* ctx, double* N_t, double* escaped, size_t nsteps) {
+  if (!ctx) return TRINITY_E_INVALID;
+  if (nsteps > static_cast<size_t>(ctx->steps_done)) return fail(ctx, TRINITY_E_INVALID, "more steps than done");
+  if (nsteps == 0) return TRINITY_OK;
+  const size_t first = ctx->steps_done - nsteps;
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (N_t) CK(cudaMemcpy(N_t, ctx->d_energy + first, nsteps * sizeof(double), cudaMemcpyDeviceToHost));
+  if (escaped) CK(cudaMemcpy(escaped, ctx->d_escaped + first, nsteps * sizeof(double), cudaMemcpyDeviceToHost));
+  return TRINITY_OK;
+}
+
+int trinity_read_iterations(trinity_ctx* ctx, int* iters_max, double* iters_mean, size_t nsteps) {
+  if (!ctx) return TRINITY_E_INVALID;
+  if (nsteps > static_cast<size_t>(ctx->steps_done)) return fail(ctx, TRINITY_E_INVALID, "more steps than done");
+  if (nsteps == 0) return TRINITY_OK;
+  const size_t first = ctx->steps_done - nsteps;
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (iters_max) CK(cudaMemcpy(iters_max, ctx->d_iters_max + first, nsteps * sizeof(int), cudaMemcpyDeviceToHost));
+  if (iters_mean) {
+    std::vector<unsigned long long> s(nsteps);
+    CK(cudaMemcpy(s.data(), ctx->d_iters_sum + first, nsteps * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    for (size_t k = 0; k < nsteps; ++k) iters_mean[k] = double(s[k]) / double(ctx->g.nv);
+  }
+  return TRINITY_OK;
+}
+
+int trinity_read_field(trinity_ctx* ctx, int what, int back, void* out, size_t bytes, int ptr_kind) {
+  if (!ctx) return TRINITY_E_INVALID;
+  const size_t cnt = static_cast<size_t>(ctx->g.na) * ctx->g.nv;
+  if ((what != TRINITY_FIELD_I && what != TRINITY_FIELD_S) || back < 0 || back > kRing - 1 ||
+      bytes != cnt * 4 || !out || (ptr_kind != 0 && ptr_kind != 1))
+    return fail(ctx, TRINITY_E_INVALID, "bad field request");
+  const int lev = ctx->steps_done - 1 - back;
+  CK(cudaStreamSynchronize(ctx->stream));
+  const cudaMemcpyKind kind = ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (lev < ctx->g.hist_from) {
+    if (ptr_kind)
+      CK(cudaMemset(out, 0, bytes));
+    else
+      std::memset(out, 0, bytes);
+    return TRINITY_OK;
+  }
+  const float* base = (what == TRINITY_FIELD_I ? ctx->I : ctx->S) + static_cast<size_t>(ring_slot(lev)) * cnt;
+  CK(cudaMemcpy(out, base, bytes, kind));
+  return TRINITY_OK;
+}
+
+int trinity_steps_done(const trinity_ctx* ctx, int* n) {
+  if (!ctx || !n) return TRINITY_E_INVALID;
+  *n = ctx->steps_done;
+  return TRINITY_OK;
+}
+
+int trinity_reset(trinity_ctx* ctx) {
+  if (!ctx) return TRINITY_E_INVALID;
+  const size_t cnt = static_cast<size_t>(ctx->g.na) * ctx->g.nv;
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemset(ctx->I, 0, kRing * cnt * 4));
+  CK(cudaMemset(ctx->S, 0, kRing * cnt * 4));
+  CK(cudaMemset(ctx->Q, 0, cnt * 4));
+  CK(cudaMemset(ctx->d_step, 0, sizeof(int)));
+  CK(cudaMemset(ctx->d_smax, 0, 2 * sizeof(unsigned)));
+  CK(cudaMemset(ctx->d_nonconv, 0, sizeof(int)));
+  CK(cudaMemset(ctx->d_error, 0, sizeof(int)));
+  if (ctx->capacity > 0) {
+    CK(cudaMemset(ctx->d_iters_max, 0, ctx->capacity * sizeof(int)));
+    CK(cudaMemset(ctx->d_iters_sum, 0, ctx->capacity * sizeof(unsigned long long)));
+    CK(cudaMemset(ctx->d_energy, 0, ctx->capacity * sizeof(double)));
+    CK(cudaMemset(ctx->d_escaped, 0, ctx->capacity * sizeof(double)));
+  }
+  if (ctx->d_det) CK(cudaMemset(ctx->d_det, 0, ctx->dets.size() * std::max(ctx->nbins, 1) * sizeof(double)));
+  ctx->g.hist_from = 0;
+  ctx->has_init = false;
+  ctx->steps_done = 0;
+  ctx->nonconv_seen = 0;
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  return TRINITY_OK;
+}
+
+const char* trinity_last_error(const trinity_ctx* ctx) {
+  if (!ctx) return "null context";
+  return ctx->err.c_str();
+}
+
+void trinity_destroy(trinity_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+  void* bufs[] = {ctx->I,         ctx->S,          ctx->Q,           ctx->mut,       ctx->alb,
+                  ctx->nidx,      ctx->P32,        ctx->Pbf,         ctx->d_dirs,    ctx->d_offs,
+                  ctx->d_det_vox, ctx->d_det_dir,  ctx->d_det_id,    ctx->d_det_w,   ctx->d_det,
+                  ctx->d_step,    ctx->d_smax,     ctx->d_nonconv,   ctx->d_error,   ctx->d_iters_max,
+                  ctx->d_iters_sum, ctx->d_energy, ctx->d_escaped,   ctx->d_bins};
+  for (void* p : bufs)
+    if (p) cudaFree(p);
+  delete ctx;
+}
+
+// ---- host-side tables ----
+
+int trinity_healpix_dirs(int nside, double* out, size_t n) {
+  if (nside < 1 || nside > 64 || !out) return TRINITY_E_INVALID;
+  const std::vector<double> d = healpix_dirs(nside);
+  if (n != d.size()) return TRINITY_E_INVALID;
+  std::copy(d.begin(), d.end(), out);
+  return TRINITY_OK;
+}
+
+int trinity_phase_matrix(int nside, double g, double* out, size_t n, double* g_eff) {
+  if (nside < 1 || nside > 8 || !out) return TRINITY_E_INVALID;
+  try {
+    const std::vector<double> P = phase_matrix(nside, g, g_eff);
+    if (n != P.size()) return TRINITY_E_INVALID;
+    std::copy(P.begin(), P.end(), out);
+  } catch (...) {
+    return TRINITY_E_INVALID;
+  }
+  return TRINITY_OK;
+}
+
+int trinity_lattice_tables(int nside, int nx, int ny, int nz, double h_mm, int periodic,
+                           int32_t* dom_sgn, double* ds, int8_t* offsets, size_t n_offsets) {
+  if (nside < 1 || nside > 64 || nx < 1 || ny < 1 || nz < 1 || !(h_mm > 0.0)) return TRINITY_E_INVALID;
+  try {
+    const Lattice L = build_lattice(healpix_dirs(nside), nx, ny, nz, h_mm, periodic != 0);
+    if (n_offsets != L.off.size()) return TRINITY_E_INVALID;
+    for (int d = 0; d < L.na; ++d) {
+      if (dom_sgn) {
+        dom_sgn[2 * d] = L.dom[d];
+        dom_sgn[2 * d + 1] = L.sgn[d];
+      }
+      if (ds) ds[d] = L.ds[d];
+    }
+    if (offsets) std::copy(L.off.begin(), L.off.end(), offsets);
+  } catch (...) {
+    return TRINITY_E_INVALID;
+  }
+  return TRINITY_OK;
+}
+
+int trinity_cone_weights(int nside, int face, double half_angle_deg, int inward, double* out, size_t n) {
+  if (nside < 1 || nside > 64 || !out) return TRINITY_E_INVALID;
+  try {
+    const std::vector<double> a = cone_weights(healpix_dirs(nside), face, half_angle_deg, inward != 0);
+    if (n != a.size()) return TRINITY_E_INVALID;
+    std::copy(a.begin(), a.end(), out);
+  } catch (...) {
+    return TRINITY_E_INVALID;
+  }
+  return TRINITY_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,102 @@
+// Device-side structures and small helpers shared by the kernels and the C-ABI layer.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace trinity {
+
+// Per-direction constants of the ray lattice (built on the host in FP64, stored FP32).
+struct DirInfo {
+  int dom;        // dominant axis 0/1/2
+  int sgn;        // travel sign along dom
+  int a0, a1;     // transverse axes (increasing order)
+  float ds;       // ray-sample spacing h / |Omega_dom| (mm)
+  float dcoef;    // ds / (c0 dt): retarded delay in steps per unit refractive index
+  float src_amp;  // inflow intensity while the pulse is on (0: not a source direction)
+  float wcos_out[6];  // w * (Omega . n_out) * h^2 * dt for faces the ray leaves (else 0)
+};
+
+struct GridParams {
+  int nx, ny, nz;
+  int nv;           // nx * ny * nz
+  int na;           // directions
+  int nmax;         // stride of the offset table
+  int periodic;
+  int hist_from;    // first valid time level: 0, or -4 with an initial state
+  int src_voxel;    // flat voxel index of the source spot, -1 if none
+  int pulse_steps;
+  float h;
+  float ds_max;     // max_d ds_d (for the contraction bound)
+  float e_scale;    // h^3 / c0 * w  (energy per unit I * n)
+};
+
+// Per-run device counters and tallies (pointers into context-owned buffers).
+struct RunState {
+  int* step;                     // current time level n (advanced by the last kernel of a step)
+  unsigned* smax;                // [2] max |S| of levels n-1 / n as float bits (ping-pong)
+  int* iters_max;                // [capacity] per step
+  unsigned long long* iters_sum; // [capacity] per step (sum over voxels)
+  double* energy;                // [capacity] photon energy in the box after the step
+  double* escaped;               // [capacity] energy leaving through the faces in the step
+  int* nonconv;                  // count of voxel-steps that hit max_iters
+  int* bins;                     // [capacity] detector bin of each step (-1: none)
+  int* error;                    // device error word (0 = ok)
+};
+
+__host__ __device__ inline int ring_slot(int level) { return ((level % 5) + 5) % 5; }
+
+// exp(-x), b0(x), b1(x) of Eq. 9: b0 = [1 - (1+x) e^-x]/x, b1 = [x - 1 + e^-x]/x.
+// For x < 1 the closed forms cancel catastrophically in FP32, so their Taylor series
+// (from the series of exp) are summed to x^11, which is exact to FP32 rounding there.
+__device__ __forceinline__ float ray_b0(float x, float T) {
+  if (x < 1.0f) {
+    float p = 1.0f / 43545600.0f;
+    p = fmaf(p, x, -1.0f / 3991680.0f);
+    p = fmaf(p, x, 1.0f / 403200.0f);
+    p = fmaf(p, x, -1.0f / 45360.0f);
+    p = fmaf(p, x, 1.0f / 5760.0f);
+    p = fmaf(p, x, -1.0f / 840.0f);
+    p = fmaf(p, x, 1.0f / 144.0f);
+    p = fmaf(p, x, -1.0f / 30.0f);
+    p = fmaf(p, x, 1.0f / 8.0f);
+    p = fmaf(p, x, -1.0f / 3.0f);
+    p = fmaf(p, x, 0.5f);
+    return p * x;
+  }
+  return (1.0f - (1.0f + x) * T) / x;
+}
+
+__device__ __forceinline__ float ray_b1(float x, float T) {
+  if (x < 1.0f) {
+    float p = 1.0f / 479001600.0f;
+    p = fmaf(p, x, -1.0f / 39916800.0f);
+    p = fmaf(p, x, 1.0f / 3628800.0f);
+    p = fmaf(p, x, -1.0f / 362880.0f);
+    p = fmaf(p, x, 1.0f / 40320.0f);
+    p = fmaf(p, x, -1.0f / 5040.0f);
+    p = fmaf(p, x, 1.0f / 720.0f);
+    p = fmaf(p, x, -1.0f / 120.0f);
+    p = fmaf(p, x, 1.0f / 24.0f);
+    p = fmaf(p, x, -1.0f / 6.0f);
+    p = fmaf(p, x, 0.5f);
+    return p * x;
+  }
+  return (x - 1.0f + T) / x;
+}
+
+// Kernel launchers (defined in kernels.cu / scatter_tc.cu).
+cudaError_t launch_sweep(const GridParams& g, const DirInfo* dirs, const int8_t* offs,
+                         const float* Iring, const float* Sring, const float* mut,
+                         const float* nidx, float* Q, RunState rs, cudaStream_t st);
+cudaError_t launch_scatter_fp32(const GridParams& g, const DirInfo* dirs, const float* P,
+                                const float* Q, const float* mut, const float* alb,
+                                const float* nidx, float* Iring, float* Sring, float tol,
+                                int max_iters, RunState rs, cudaStream_t st);
+cudaError_t launch_tally(const GridParams& g, const DirInfo* dirs, const float* Iring,
+                         const int* det_vox, const int* det_dir, const float* det_w,
+                         const int* det_id, int n_det_entries, double* det, int nbins,
+                         RunState rs, cudaStream_t st);
+cudaError_t launch_advance(RunState rs, cudaStream_t st);
+
+}  // namespace trinity

@@ -1,0 +1,245 @@
+// Host-side FP64 tables: HEALPix directions, normalised phase matrix, ray lattice,
+// cone weights.  Plain C++ on the CPU, run once per context.
+#include "host_tables.h"
+
+#include <algorithm>
+#include <cmath>
+#include <stdexcept>
+
+namespace trinity {
+
+namespace {
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kSnap = 1e-9;     // integer snap margin for floor decisions
+constexpr double kDomTie = 1e-12;  // dominant-axis tie margin
+constexpr int kCapMu = 64;         // cap sampling: rings in cos(theta)
+constexpr int kCapPhi = 256;       // cap sampling: points per ring
+}  // namespace
+
+long floor_snap(double y) {
+  const double r = std::nearbyint(y);
+  if (std::fabs(y - r) < kSnap) return static_cast<long>(r);
+  return static_cast<long>(std::floor(y));
+}
+
+// HEALPix (Gorski et al. 2005) pixel centres, RING order (Section 2.1 of the paper:
+// equal-area angular bins).  Ring i = 1 .. 4N-1 from the north pole.  Polar-cap rings
+// hold 4i pixels at z = 1 - i^2/(3N^2), phi = (pi/2i)(j - 1/2); belt rings hold 4N
+// pixels at z = 4/3 - 2i/(3N), phi = (pi/2N)(j - s/2) with s = (i - N + 1) mod 2; the
+// southern cap mirrors the northern one.
+std::vector<double> healpix_dirs(int nside) {
+  if (nside < 1) throw std::runtime_error("nside must be >= 1");
+  const int npix = 12 * nside * nside;
+  std::vector<double> out;
+  out.reserve(3 * static_cast<size_t>(npix));
+  const double N = nside;
+  for (int i = 1; i < 4 * nside; ++i) {
+    double z;
+    int count;
+    double dphi, shift;
+    if (i < nside) {
+      z = 1.0 - double(i) * i / (3.0 * N * N);
+      count = 4 * i;
+      dphi = kPi / (2.0 * i);
+      shift = 0.5;
+    } else if (i <= 3 * nside) {
+      z = 4.0 / 3.0 - 2.0 * i / (3.0 * N);
+      count = 4 * nside;
+      dphi = kPi / (2.0 * N);
+      shift = 0.5 * ((i - nside + 1) % 2);
+    } else {
+      const int k = 4 * nside - i;
+      z = -(1.0 - double(k) * k / (3.0 * N * N));
+      count = 4 * k;
+      dphi = kPi / (2.0 * k);
+      shift = 0.5;
+    }
+    const double st = std::sqrt((1.0 - z) * (1.0 + z));
+    for (int j = 1; j <= count; ++j) {
+      const double phi = dphi * (j - shift);
+      out.push_back(st * std::cos(phi));
+      out.push_back(st * std::sin(phi));
+      out.push_back(z);
+    }
+  }
+  return out;
+}
+
+namespace {
+
+// Eq. 11: Henyey-Greenstein phase function per steradian.
+double hg(double mu, double g) {
+  const double q = 1.0 + g * g - 2.0 * g * mu;
+  return (1.0 - g * g) / (4.0 * kPi * q * std::sqrt(q));
+}
+
+// K_ij = w * HG(Omega_i . Omega_j; g), scaled to unit row (= column) sums by a symmetric
+// diagonal D (damped Sinkhorn: d <- sqrt(d / (K d))), then returned as D K D.
+std::vector<double> scaled_kernel(const std::vector<double>& dirs, double g) {
+  const int n = static_cast<int>(dirs.size() / 3);
+  const double w = 4.0 * kPi / n;
+  std::vector<double> K(static_cast<size_t>(n) * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double mu = dirs[3 * i] * dirs[3 * j] + dirs[3 * i + 1] * dirs[3 * j + 1] +
+                  dirs[3 * i + 2] * dirs[3 * j + 2];
+      mu = std::min(1.0, std::max(-1.0, mu));
+      K[static_cast<size_t>(i) * n + j] = w * hg(mu, g);
+    }
+  std::vector<double> d(n, 1.0), Kd(n);
+  for (int it = 0; it < 200000; ++it) {
+    for (int i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (int j = 0; j < n; ++j) s += K[static_cast<size_t>(i) * n + j] * d[j];
+      Kd[i] = s;
+    }
+    double err = 0.0;
+    for (int i = 0; i < n; ++i) err = std::max(err, std::fabs(d[i] * Kd[i] - 1.0));
+    if (err < 1e-14) break;
+    if (it == 199999) throw std::runtime_error("phase-matrix scaling did not converge");
+    for (int i = 0; i < n; ++i) d[i] = std::sqrt(d[i] / Kd[i]);
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) K[static_cast<size_t>(i) * n + j] *= d[i] * d[j];
+  return K;
+}
+
+double mean_cos(const std::vector<double>& P, const std::vector<double>& dirs) {
+  const int n = static_cast<int>(dirs.size() / 3);
+  double tot = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double row = 0.0;
+    for (int j = 0; j < n; ++j) {
+      const double mu = dirs[3 * i] * dirs[3 * j] + dirs[3 * i + 1] * dirs[3 * j + 1] +
+                        dirs[3 * i + 2] * dirs[3 * j + 2];
+      row += P[static_cast<size_t>(i) * n + j] * mu;
+    }
+    tot += row;
+  }
+  return tot / n;
+}
+
+}  // namespace
+
+// Eq. 12 with a normalised discrete kernel: P = D K(g_eff) D, unit row and column sums,
+// g_eff chosen by bisection so that the mean scattering cosine of P equals g.
+std::vector<double> phase_matrix(int nside, double g, double* g_eff) {
+  if (!(g > -1.0 && g < 1.0)) throw std::runtime_error("g must lie in (-1, 1)");
+  const std::vector<double> dirs = healpix_dirs(nside);
+  const int n = static_cast<int>(dirs.size() / 3);
+  if (g == 0.0) {
+    if (g_eff) *g_eff = 0.0;
+    return std::vector<double>(static_cast<size_t>(n) * n, 1.0 / n);
+  }
+  double lo = g > 0 ? 0.0 : -1.0 + 1e-12;
+  double hi = g > 0 ? 1.0 - 1e-12 : 0.0;
+  for (int it = 0; it < 200 && hi - lo >= 1e-15; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mean_cos(scaled_kernel(dirs, mid), dirs) < g)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  const double ge = 0.5 * (lo + hi);
+  if (g_eff) *g_eff = ge;
+  return scaled_kernel(dirs, ge);
+}
+
+// Slab-lattice long rays (Section 2.1: rays laid independently of the grid, each grid
+// point takes the nearest ray; Section 2.4 step 1).  Dominant axis = largest |Omega|
+// component (ties: z, then y, then x); slab k' counted along the travel direction;
+// the ray through a slab-0 voxel centre sits in column c + floor(1/2 + k' t) at slab k',
+// t = Omega_a / |Omega_dom|, so the upwind sample of a slab-k' voxel is shifted by
+// Delta(k') = floor(1/2 + k' t) - floor(1/2 + (k'-1) t) in {-1, 0, 1}.
+Lattice build_lattice(const std::vector<double>& dirs, int nx, int ny, int nz, double h,
+                      bool periodic) {
+  Lattice L;
+  L.na = static_cast<int>(dirs.size() / 3);
+  const int n[3] = {nx, ny, nz};
+  L.nmax = std::max(nx, std::max(ny, nz));
+  L.dom.resize(L.na);
+  L.sgn.resize(L.na);
+  L.ds.resize(L.na);
+  L.off.assign(static_cast<size_t>(L.na) * 2 * L.nmax, 0);
+  for (int d = 0; d < L.na; ++d) {
+    const double om[3] = {dirs[3 * d], dirs[3 * d + 1], dirs[3 * d + 2]};
+    const double ax = std::fabs(om[0]), ay = std::fabs(om[1]), az = std::fabs(om[2]);
+    int dom;
+    if (az >= std::max(ax, ay) - kDomTie)
+      dom = 2;
+    else if (ay >= ax - kDomTie)
+      dom = 1;
+    else
+      dom = 0;
+    L.dom[d] = dom;
+    L.sgn[d] = om[dom] > 0 ? 1 : -1;
+    L.ds[d] = h / std::fabs(om[dom]);
+    int j = 0;
+    for (int a = 0; a < 3; ++a) {
+      if (a == dom) continue;
+      const double t = om[a] / std::fabs(om[dom]);
+      for (int k = 0; k < n[dom]; ++k) {
+        long delta = floor_snap(0.5 + k * t) - floor_snap(0.5 + (k - 1.0) * t);
+        if (k == 0 && !periodic) delta = 0;
+        if (delta < -1 || delta > 1) throw std::runtime_error("lattice offset out of range");
+        L.off[(static_cast<size_t>(d) * 2 + j) * L.nmax + k] = static_cast<int8_t>(delta);
+      }
+      ++j;
+    }
+  }
+  return L;
+}
+
+// 15-degree collimation of the pulse and the detectors (Section 3.1).  The cap around
+// the face normal is sampled at kCapMu x kCapPhi equal-area points (cos theta uniform,
+// phi uniform, both at cell midpoints) in the frame (e_u, e_v, normal); each point goes
+// to the direction with the largest dot product; the weight of a direction is its share
+// of the points.  Two best dot products closer than 1e-12 would make the assignment
+// depend on rounding, so that raises.
+std::vector<double> cone_weights(const std::vector<double>& dirs, int face,
+                                 double half_angle_deg, bool inward) {
+  if (face < 0 || face > 5) throw std::runtime_error("face must be 0..5");
+  if (!(half_angle_deg > 0.0 && half_angle_deg < 90.0))
+    throw std::runtime_error("cone half-angle must lie in (0, 90) degrees");
+  const int na = static_cast<int>(dirs.size() / 3);
+  const int ax = face / 2;
+  const double out_sign = (face % 2 == 0) ? -1.0 : 1.0;
+  double nrm[3] = {0, 0, 0}, eu[3] = {0, 0, 0}, ev[3] = {0, 0, 0};
+  nrm[ax] = inward ? -out_sign : out_sign;
+  int uv[2], j = 0;
+  for (int a = 0; a < 3; ++a)
+    if (a != ax) uv[j++] = a;
+  eu[uv[0]] = 1.0;
+  ev[uv[1]] = 1.0;
+  const double ct = std::cos(half_angle_deg * kPi / 180.0);
+  std::vector<long> count(na, 0);
+  for (int k = 0; k < kCapMu; ++k) {
+    const double mu = 1.0 - (k + 0.5) * (1.0 - ct) / kCapMu;
+    const double st = std::sqrt((1.0 - mu) * (1.0 + mu));
+    for (int l = 0; l < kCapPhi; ++l) {
+      const double phi = 2.0 * kPi * (l + 0.5) / kCapPhi;
+      const double cp = std::cos(phi), sp = std::sin(phi);
+      double p[3];
+      for (int a = 0; a < 3; ++a) p[a] = mu * nrm[a] + st * cp * eu[a] + st * sp * ev[a];
+      double best = -2.0, second = -2.0;
+      int arg = -1;
+      for (int d = 0; d < na; ++d) {
+        const double dot = p[0] * dirs[3 * d] + p[1] * dirs[3 * d + 1] + p[2] * dirs[3 * d + 2];
+        if (dot > best) {
+          second = best;
+          best = dot;
+          arg = d;
+        } else if (dot > second) {
+          second = dot;
+        }
+      }
+      if (best - second < 1e-12) throw std::runtime_error("cone sample equidistant from two directions");
+      ++count[arg];
+    }
+  }
+  std::vector<double> alpha(na);
+  for (int d = 0; d < na; ++d) alpha[d] = double(count[d]) / double(kCapMu * kCapPhi);
+  return alpha;
+}
+
+}  // namespace trinity

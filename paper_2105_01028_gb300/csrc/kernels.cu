@@ -1,0 +1,437 @@
+// FP32 kernels of one time step: the ray sweep (Eq. 10 without its S(n) term), the
+// per-voxel source iteration on CUDA cores (Eq. 12, Section 2.4 steps 5-6), the
+// detector / escape tallies (Section 3.1) and the step counter.
+#include <cfloat>
+#include <cstdint>
+
+#include "device.cuh"
+
+namespace trinity {
+
+namespace {
+
+__device__ __forceinline__ int pick(int axis, int x, int y, int z) {
+  return axis == 0 ? x : (axis == 1 ? y : z);
+}
+
+// ----------------------------------------------------------------------------------------
+// Sweep: Q(v, d) = I_up exp(-x) + S_up b0(x), the known part of Eq. 10 at time level n.
+// One thread per (voxel, direction); blockIdx.y = direction, threads run along x so the
+// loads of the upwind plane (shifted by at most one voxel) coalesce.
+// The upwind sample of v is the previous point of its long ray (slab lattice, Section
+// 2.1): one slab back along dom(d), shifted by the per-slab offsets.  Its I and S are
+// taken at the retarded time n - delta, delta = ds n(v) / (c0 dt), linearly
+// interpolated between the stored levels n - m and n - m - 1 (m = floor(delta)).
+// ----------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) sweep_kernel(GridParams g, const DirInfo* __restrict__ dirs,
+                                                    const int8_t* __restrict__ offs,
+                                                    const float* __restrict__ Iring,
+                                                    const float* __restrict__ Sring,
+                                                    const float* __restrict__ mut,
+                                                    const float* __restrict__ nidx,
+                                                    float* __restrict__ Q, RunState rs) {
+  const int n = *rs.step;
+  const int d = blockIdx.y;
+  if (d == 0 && blockIdx.x == 0 && threadIdx.x == 0) rs.smax[n & 1] = 0u;
+  const DirInfo di = dirs[d];
+  const size_t plane = static_cast<size_t>(g.nv);
+  const int8_t* off0 = offs + (static_cast<size_t>(d) * 2 + 0) * g.nmax;
+  const int8_t* off1 = offs + (static_cast<size_t>(d) * 2 + 1) * g.nmax;
+  const int nd = pick(di.dom, g.nx, g.ny, g.nz);
+  const int n0 = pick(di.a0, g.nx, g.ny, g.nz);
+  const int n1 = pick(di.a1, g.nx, g.ny, g.nz);
+  const int sd = di.dom == 0 ? 1 : (di.dom == 1 ? g.nx : g.nx * g.ny);
+  const int s0 = di.a0 == 0 ? 1 : (di.a0 == 1 ? g.nx : g.nx * g.ny);
+  const int s1 = di.a1 == 0 ? 1 : (di.a1 == 1 ? g.nx : g.nx * g.ny);
+
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < g.nv; v += gridDim.x * blockDim.x) {
+    const int x = v % g.nx;
+    const int t = v / g.nx;
+    const int y = t % g.ny;
+    const int z = t / g.ny;
+    const int pd = pick(di.dom, x, y, z);
+    const int p0 = pick(di.a0, x, y, z);
+    const int p1 = pick(di.a1, x, y, z);
+    const int kp = di.sgn > 0 ? pd : nd - 1 - pd;
+    int qd = pd - di.sgn;
+    int q0 = p0 - off0[kp];
+    int q1 = p1 - off1[kp];
+    int kind = 0;  // 0: upwind inside, 1: inflow face, 2: entered through a side face
+    if (g.periodic) {
+      qd = (qd + nd) % nd;
+      q0 = (q0 + n0) % n0;
+      q1 = (q1 + n1) % n1;
+    } else if (kp == 0) {
+      kind = 1;
+    } else if (q0 < 0 || q0 >= n0 || q1 < 0 || q1 >= n1) {
+      kind = 2;
+    }
+    const float delta = di.dcoef * nidx[v];
+    const int m = static_cast<int>(floorf(delta));
+    const float f = delta - static_cast<float>(m);
+    const int L0 = n - m, L1 = n - m - 1;
+    float Iup = 0.0f, Sup = 0.0f;
+    if (kind == 0) {
+      const size_t u = static_cast<size_t>(qd) * sd + static_cast<size_t>(q0) * s0 +
+                       static_cast<size_t>(q1) * s1;
+      float i0 = 0.0f, i1 = 0.0f, s0v = 0.0f, s1v = 0.0f;
+      if (L0 >= g.hist_from) {
+        const size_t o = (static_cast<size_t>(ring_slot(L0)) * g.na + d) * plane + u;
+        i0 = __ldg(Iring + o);
+        s0v = __ldg(Sring + o);
+      }
+      if (L1 >= g.hist_from) {
+        const size_t o = (static_cast<size_t>(ring_slot(L1)) * g.na + d) * plane + u;
+        i1 = __ldg(Iring + o);
+        s1v = __ldg(Sring + o);
+      }
+      Iup = (1.0f - f) * i0 + f * i1;
+      Sup = (1.0f - f) * s0v + f * s1v;
+    } else if (kind == 1 && v == g.src_voxel && di.src_amp != 0.0f) {
+      const float on0 = (L0 >= 0 && L0 < g.pulse_steps) ? 1.0f : 0.0f;
+      const float on1 = (L1 >= 0 && L1 < g.pulse_steps) ? 1.0f : 0.0f;
+      Iup = di.src_amp * ((1.0f - f) * on0 + f * on1);
+    }
+    const float xo = mut[v] * di.ds;
+    const float T = expf(-xo);
+    Q[static_cast<size_t>(d) * plane + v] = Iup * T + Sup * ray_b0(xo, T);
+  }
+}
+
+// ----------------------------------------------------------------------------------------
+// Source iteration on CUDA cores (plain FP32 mode).
+// A CTA owns a tile of 32 voxels; thread i < NA owns outgoing direction i of all 32.
+// Per iteration: Y[v][i] = sum_j P[i][j] X[v][j] (P symmetric, read as P[j][i] so a warp
+// reads a contiguous row), S_new = a Y, X = Q + b1 S.  The per-voxel stop test needs the
+// max over directions of |S_new - S_old| and |S_new|: a warp "transpose" reduction leaves
+// lane v holding the warp's maximum for voxel v, then the warps combine through smem.
+// ----------------------------------------------------------------------------------------
+constexpr int kTile = 32;
+constexpr int kXStride = kTile + 4;  // padded row (floats) of the X tile in smem
+
+template <int NA>
+struct ScatterCfg {
+  static constexpr int kThreads = ((NA + 31) / 32) * 32;
+  static constexpr int kWarps = kThreads / 32;
+};
+
+// After the call lane l holds max over the warp's lanes of vals[l] (vals[0] on return).
+__device__ __forceinline__ float warp_transpose_max(float (&vals)[32], int lane) {
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const bool upper = (lane & s) != 0;
+#pragma unroll
+    for (int k = 0; k < s; ++k) {
+      const float send = upper ? vals[k] : vals[k + s];
+      const float keep = upper ? vals[k + s] : vals[k];
+      const float recv = __shfl_xor_sync(0xffffffffu, send, s);
+      vals[k] = fmaxf(keep, recv);
+    }
+  }
+  return vals[0];
+}
+
+template <int NA>
+__global__ void __launch_bounds__(ScatterCfg<NA>::kThreads)
+    scatter_fp32_kernel(GridParams g, const DirInfo* __restrict__ dirs, const float* __restrict__ P,
+                        const float* __restrict__ Q, const float* __restrict__ mut,
+                        const float* __restrict__ alb, const float* __restrict__ nidx,
+                        float* __restrict__ Iring, float* __restrict__ Sring, float tol,
+                        int max_iters, RunState rs) {
+  constexpr int W = ScatterCfg<NA>::kWarps;
+  __shared__ __align__(16) float Xs[2][NA][kXStride];
+  __shared__ float red_d[W][kTile];
+  __shared__ float red_s[W][kTile];
+  __shared__ float a_s[kTile], rho_s[kTile];
+  __shared__ int iters_s[kTile];
+  __shared__ unsigned act_s;
+
+  const int n = *rs.step;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int i = tid;  // outgoing direction
+  const bool live = i < NA;
+  const int v0 = blockIdx.x * kTile;
+  const size_t plane = static_cast<size_t>(g.nv);
+  const float s_glob = __uint_as_float(rs.smax[(n - 1) & 1]);
+
+  if (tid < kTile) {
+    const int v = v0 + tid;
+    float a = 0.0f, rho = 0.0f;
+    if (v < g.nv) {
+      a = alb[v];
+      const float xm = mut[v] * g.ds_max;
+      rho = a * ray_b1(xm, expf(-xm));  // b1 grows with x: max over d is at ds_max
+    }
+    a_s[tid] = a;
+    rho_s[tid] = rho;
+    iters_s[tid] = 0;
+  }
+  if (tid == 0) act_s = (g.nv - v0 >= kTile) ? 0xffffffffu : ((1u << (g.nv - v0)) - 1u);
+  __syncthreads();
+
+  float q[kTile], b1[kTile], so[kTile], acc[kTile];
+  const float ds = live ? dirs[i].ds : 0.0f;
+  const bool has_prev = (n - 1) >= g.hist_from;
+  const size_t prev_off = (static_cast<size_t>(ring_slot(n - 1)) * g.na + (live ? i : 0)) * plane;
+#pragma unroll
+  for (int v = 0; v < kTile; ++v) {
+    const int vv = v0 + v;
+    const bool ok = live && vv < g.nv;
+    q[v] = ok ? __ldg(Q + static_cast<size_t>(i) * plane + vv) : 0.0f;
+    const float xo = ok ? mut[vv] * ds : 0.0f;
+    b1[v] = ok ? ray_b1(xo, expf(-xo)) : 0.0f;
+    so[v] = (ok && has_prev) ? Sring[prev_off + vv] : 0.0f;
+  }
+  if (live) {
+#pragma unroll
+    for (int v = 0; v < kTile; v += 4) {
+      float4 x4 = make_float4(q[v] + b1[v] * so[v], q[v + 1] + b1[v + 1] * so[v + 1],
+                              q[v + 2] + b1[v + 2] * so[v + 2], q[v + 3] + b1[v + 3] * so[v + 3]);
+      *reinterpret_cast<float4*>(&Xs[0][i][v]) = x4;
+    }
+  }
+  unsigned act = act_s;
+  int cur = 0;
+  int k = 0;
+  while (act != 0u && k < max_iters) {
+    ++k;
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < kTile; ++v) acc[v] = 0.0f;
+    if (live) {
+      const float* pcol = P + i;
+#pragma unroll 4
+      for (int j = 0; j < NA; ++j) {
+        const float p = __ldg(pcol + static_cast<size_t>(j) * NA);
+        const float4* xr = reinterpret_cast<const float4*>(&Xs[cur][j][0]);
+#pragma unroll
+        for (int v4 = 0; v4 < kTile / 4; ++v4) {
+          const float4 x4 = xr[v4];
+          acc[4 * v4 + 0] = fmaf(p, x4.x, acc[4 * v4 + 0]);
+          acc[4 * v4 + 1] = fmaf(p, x4.y, acc[4 * v4 + 1]);
+          acc[4 * v4 + 2] = fmaf(p, x4.z, acc[4 * v4 + 2]);
+          acc[4 * v4 + 3] = fmaf(p, x4.w, acc[4 * v4 + 3]);
+        }
+      }
+    }
+    // epilogue: S_new = a * acc on active voxels; X = Q + b1 * S for the next iteration
+    float dsv[kTile], smv[kTile];
+#pragma unroll
+    for (int v = 0; v < kTile; ++v) {
+      const bool on = live && ((act >> v) & 1u);
+      const float sn = a_s[v] * acc[v];
+      dsv[v] = on ? fabsf(sn - so[v]) : 0.0f;
+      smv[v] = on ? fabsf(sn) : 0.0f;
+      so[v] = on ? sn : so[v];
+    }
+    const int nxt = cur ^ 1;
+    if (live) {
+#pragma unroll
+      for (int v = 0; v < kTile; v += 4) {
+        float4 x4 = make_float4(q[v] + b1[v] * so[v], q[v + 1] + b1[v + 1] * so[v + 1],
+                                q[v + 2] + b1[v + 2] * so[v + 2], q[v + 3] + b1[v + 3] * so[v + 3]);
+        *reinterpret_cast<float4*>(&Xs[nxt][i][v]) = x4;
+      }
+    }
+    red_d[warp][lane] = warp_transpose_max(dsv, lane);
+    red_s[warp][lane] = warp_transpose_max(smv, lane);
+    __syncthreads();
+    if (tid < kTile) {
+      const int v = tid;
+      unsigned done = 0u;
+      if ((act >> v) & 1u) {
+        float D = 0.0f, Sm = 0.0f;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          D = fmaxf(D, red_d[w][v]);
+          Sm = fmaxf(Sm, red_s[w][v]);
+        }
+        const float r = rho_s[v];
+        const float scale = fmaxf(Sm, 1e-6f * s_glob);
+        // stop: error bound within tol, or the change is at FP32 resolution (~4 ulp)
+        const bool stop = (r / (1.0f - r)) * D <= tol * scale || D <= 2.384185791e-7f * Sm;
+        if (stop) {
+          done = 1u;
+          iters_s[v] = k;
+        }
+      }
+      const unsigned mask = __ballot_sync(0xffffffffu, done);
+      if (tid == 0) act_s = act & ~mask;
+    }
+    __syncthreads();
+    act = act_s;
+    cur = nxt;
+  }
+  // voxels still active hit max_iters
+  if (tid < kTile && ((act >> tid) & 1u)) {
+    iters_s[tid] = k;
+    atomicAdd(rs.nonconv, 1);
+  }
+
+  // write I(n) = Q + b1 S, S(n); tallies
+  const size_t cur_off = (static_cast<size_t>(ring_slot(n)) * g.na + (live ? i : 0)) * plane;
+  float esum = 0.0f, smax = 0.0f;
+  if (live) {
+#pragma unroll
+    for (int v = 0; v < kTile; ++v) {
+      const int vv = v0 + v;
+      if (vv < g.nv) {
+        const float Iv = q[v] + b1[v] * so[v];
+        Iring[cur_off + vv] = Iv;
+        Sring[cur_off + vv] = so[v];
+        esum = fmaf(Iv, nidx[vv], esum);
+        smax = fmaxf(smax, fabsf(so[v]));
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    esum += __shfl_xor_sync(0xffffffffu, esum, o);
+    smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+  }
+  __syncthreads();
+  if (lane == 0) {
+    red_d[warp][0] = esum;
+    red_s[warp][0] = smax;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double e = 0.0;
+    float sm = 0.0f;
+    for (int w = 0; w < W; ++w) {
+      e += red_d[w][0];
+      sm = fmaxf(sm, red_s[w][0]);
+    }
+    atomicAdd(rs.energy + n, e * static_cast<double>(g.e_scale));
+    atomicMax(rs.smax + (n & 1), __float_as_uint(sm));
+    int im = 0;
+    unsigned long long is = 0;
+    for (int v = 0; v < kTile && v0 + v < g.nv; ++v) {
+      im = max(im, iters_s[v]);
+      is += static_cast<unsigned long long>(iters_s[v]);
+    }
+    atomicMax(rs.iters_max + n, im);
+    atomicAdd(rs.iters_sum + n, is);
+  }
+}
+
+// ----------------------------------------------------------------------------------------
+// Tallies of level n (Section 3.1): detector curves (FP64 bins) and the energy leaving
+// through all faces.  Block 0 handles the detector entry list; the other blocks cover
+// the face voxels (blockIdx.y = face).
+// ----------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) tally_kernel(GridParams g, const DirInfo* __restrict__ dirs,
+                                                    const float* __restrict__ Iring,
+                                                    const int* __restrict__ det_vox,
+                                                    const int* __restrict__ det_dir,
+                                                    const float* __restrict__ det_w,
+                                                    const int* __restrict__ det_id, int n_entries,
+                                                    double* __restrict__ det, int nbins, RunState rs) {
+  __shared__ double red[8];
+  const int n = *rs.step;
+  const size_t plane = static_cast<size_t>(g.nv);
+  const float* Icur = Iring + static_cast<size_t>(ring_slot(n)) * g.na * plane;
+  const int face = blockIdx.y;
+  if (face == 6) {
+    // detector entries: weight already holds alpha * Omega_cap * cos * h^2 * dt
+    const int b = rs.bins[n];
+    if (b < 0 || b >= nbins) return;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_entries; e += gridDim.x * blockDim.x) {
+      const double val = static_cast<double>(det_w[e]) *
+                         static_cast<double>(Icur[static_cast<size_t>(det_dir[e]) * plane + det_vox[e]]);
+      atomicAdd(det + static_cast<size_t>(det_id[e]) * nbins + b, val);
+    }
+    return;
+  }
+  if (g.periodic) return;
+  const int ax = face >> 1;
+  const int ua = ax == 0 ? 1 : 0;
+  const int va = ax == 2 ? 1 : 2;
+  const int nu = pick(ua, g.nx, g.ny, g.nz);
+  const int nvv = pick(va, g.nx, g.ny, g.nz);
+  const int pa = (face & 1) ? pick(ax, g.nx, g.ny, g.nz) - 1 : 0;
+  double acc = 0.0;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nu * nvv; t += gridDim.x * blockDim.x) {
+    const int iu = t % nu, iv = t / nu;
+    int c[3];
+    c[ax] = pa;
+    c[ua] = iu;
+    c[va] = iv;
+    const size_t v = (static_cast<size_t>(c[2]) * g.ny + c[1]) * g.nx + c[0];
+    float s = 0.0f;
+    for (int d = 0; d < g.na; ++d) {
+      const float wc = dirs[d].wcos_out[face];
+      if (wc != 0.0f) s = fmaf(wc, Icur[static_cast<size_t>(d) * plane + v], s);
+    }
+    acc += static_cast<double>(s);
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) s += red[w];
+    atomicAdd(rs.escaped + n, s);
+  }
+}
+
+__global__ void advance_kernel(RunState rs) { *rs.step += 1; }
+
+}  // namespace
+
+cudaError_t launch_sweep(const GridParams& g, const DirInfo* dirs, const int8_t* offs,
+                         const float* Iring, const float* Sring, const float* mut,
+                         const float* nidx, float* Q, RunState rs, cudaStream_t st) {
+  const int threads = 256;
+  const int bx = (g.nv + threads - 1) / threads;
+  dim3 grid(bx, g.na);
+  sweep_kernel<<<grid, threads, 0, st>>>(g, dirs, offs, Iring, Sring, mut, nidx, Q, rs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_fp32(const GridParams& g, const DirInfo* dirs, const float* P,
+                                const float* Q, const float* mut, const float* alb,
+                                const float* nidx, float* Iring, float* Sring, float tol,
+                                int max_iters, RunState rs, cudaStream_t st) {
+  const int tiles = (g.nv + kTile - 1) / kTile;
+  switch (g.na) {
+    case 12:
+      scatter_fp32_kernel<12><<<tiles, ScatterCfg<12>::kThreads, 0, st>>>(
+          g, dirs, P, Q, mut, alb, nidx, Iring, Sring, tol, max_iters, rs);
+      break;
+    case 48:
+      scatter_fp32_kernel<48><<<tiles, ScatterCfg<48>::kThreads, 0, st>>>(
+          g, dirs, P, Q, mut, alb, nidx, Iring, Sring, tol, max_iters, rs);
+      break;
+    case 192:
+      scatter_fp32_kernel<192><<<tiles, ScatterCfg<192>::kThreads, 0, st>>>(
+          g, dirs, P, Q, mut, alb, nidx, Iring, Sring, tol, max_iters, rs);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tally(const GridParams& g, const DirInfo* dirs, const float* Iring,
+                         const int* det_vox, const int* det_dir, const float* det_w,
+                         const int* det_id, int n_det_entries, double* det, int nbins,
+                         RunState rs, cudaStream_t st) {
+  const int maxface = g.nx * g.ny > g.ny * g.nz ? (g.nx * g.ny > g.nx * g.nz ? g.nx * g.ny : g.nx * g.nz)
+                                                 : (g.ny * g.nz > g.nx * g.nz ? g.ny * g.nz : g.nx * g.nz);
+  int bx = (maxface + 255) / 256;
+  if (bx > 64) bx = 64;
+  dim3 grid(bx, 7);
+  tally_kernel<<<grid, 256, 0, st>>>(g, dirs, Iring, det_vox, det_dir, det_w, det_id,
+                                     n_det_entries, det, nbins, rs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance(RunState rs, cudaStream_t st) {
+  advance_kernel<<<1, 1, 0, st>>>(rs);
+  return cudaGetLastError();
+}
+
+}  // namespace trinity

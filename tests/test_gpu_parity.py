@@ -1,0 +1,235 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (FP32 mode).  The GPU stops its source iteration when its error bound
+reaches tol = 1e-6 relative (or FP32 resolution), the oracle is run to 1e-10, and FP32
+rounding of the ~200-term angular sums adds ~1e-7 relative per iteration, damped by the
+contraction; fields and detector curves are therefore required to agree to 1e-5
+relative to their peak (detector bins below 1e-6 of the peak are not compared
+relatively).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+
+
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2105_01028_gb300 as T
+    return T
+
+
+def _oracle(prob, steps, tol=1e-10, init=None):
+    from oracle.solver import Solver
+    p = dict(prob)
+    p["tol"] = tol
+    s = Solver(p, init=init)
+    s.run(steps)
+    return s
+
+
+def _rel_peak(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _check_detectors(got, ref, tol):
+    peak = np.abs(ref).max()
+    assert peak > 0
+    assert _rel_peak(got, ref) <= tol
+    big = np.abs(ref) > 1e-6 * peak
+    rel = np.abs(got[big] - ref[big]) / np.abs(ref[big])
+    assert rel.max() <= 50 * tol, rel.max()
+
+
+@pytest.fixture(scope="module")
+def small_run():
+    T = _gpu()
+    prob = W.config_small(steps=100)
+    fwd = T.Forward(prob)
+    iters = fwd.step(100)
+    out = dict(det=fwd.detectors(), energy=fwd.energy(), I=fwd.field(T.FIELD_I),
+               S=fwd.field(T.FIELD_S), I1=fwd.field(T.FIELD_I, back=1), iters=iters,
+               iters_mean=fwd.iterations()[1])
+    fwd.close()
+    ref = _oracle(prob, 100)
+    return out, ref
+
+
+def test_small_config_detectors(small_run):
+    out, ref = small_run
+    _check_detectors(out["det"], ref.det, FP32_TOL)
+
+
+def test_small_config_energy_tallies(small_run):
+    out, ref = small_run
+    N, esc = out["energy"]
+    assert _rel_peak(N, np.array(ref.energy)) <= FP32_TOL
+    assert _rel_peak(esc, np.array(ref.escaped)) <= FP32_TOL
+
+
+def test_small_config_fields_elementwise(small_run):
+    out, ref = small_run
+    assert _rel_peak(out["I"], ref.level("I")) <= FP32_TOL
+    assert _rel_peak(out["S"], ref.level("S")) <= FP32_TOL
+    assert _rel_peak(out["I1"], ref.level("I", back=1)) <= FP32_TOL
+
+
+def test_small_config_iteration_counts_plausible(small_run):
+    out, ref = small_run
+    # same stop rule, looser tolerance on the GPU (1e-6 vs the oracle's 1e-10)
+    assert np.all(out["iters"] >= 1)
+    assert np.all(out["iters"][2:] <= np.array(ref.iters_max)[2:] + 5)
+
+
+@pytest.mark.parametrize("shape,nside,steps", [((13, 11, 9), 2, 30), ((9, 7, 12), 4, 24),
+                                              ((6, 5, 4), 1, 20)])
+def test_ragged_grids(shape, nside, steps):
+    """Grids whose voxel count is not a multiple of the 32-voxel tile, every angular
+    resolution, a source on a side face and detectors on several faces."""
+    T = _gpu()
+    nx, ny, nz = shape
+    prob = W.homogeneous(nx, ny, nz, nside, 0.02, 3.0, steps=steps)
+    prob["source"] = dict(face=2, u_mm=nx / 2, v_mm=nz / 2, half_angle_deg=15.0, pulse_steps=2,
+                          energy=1.0)
+    prob["detectors"] = [dict(face=2, u_mm=nx / 2 + 2.5, v_mm=nz / 2, radius_mm=1.2, half_angle_deg=15.0),
+                         dict(face=3, u_mm=nx / 2, v_mm=nz / 2, radius_mm=2.0, half_angle_deg=20.0)]
+    prob["nbins"] = steps // 4 + 2
+    fwd = T.Forward(prob)
+    fwd.step(steps)
+    ref = _oracle(prob, steps)
+    assert _rel_peak(fwd.field(T.FIELD_I), ref.level("I")) <= FP32_TOL
+    assert _rel_peak(fwd.field(T.FIELD_S), ref.level("S")) <= FP32_TOL
+    _check_detectors(fwd.detectors(), ref.det, FP32_TOL)
+    fwd.close()
+
+
+def test_heterogeneous_optics_small():
+    """Air cylinder (n = 1, no scattering) and absorbing spheres at a quarter of the
+    heterogeneous workload's size: per-voxel delays, albedo zero, strong absorbers."""
+    T = _gpu()
+    prob = W.config_hetero(steps=30, precision="fp32", nx=32, ny=32, nz=24, nside=2, scale=0.25)
+    fwd = T.Forward(prob)
+    fwd.step(30)
+    ref = _oracle(prob, 30)
+    assert _rel_peak(fwd.field(T.FIELD_I), ref.level("I")) <= FP32_TOL
+    _check_detectors(fwd.detectors(), ref.det, FP32_TOL)
+    fwd.close()
+
+
+def test_periodic_isotropic_invariance_on_gpu():
+    T = _gpu()
+    prob = W.homogeneous(8, 6, 5, 2, 0.0, 7.0, boundary="periodic", steps=10)
+    fwd = T.Forward(prob)
+    ones = np.ones((48, 8 * 6 * 5), dtype=np.float32)
+    fwd.set_initial_state(ones, ones)
+    fwd.step(10)
+    np.testing.assert_allclose(fwd.field(T.FIELD_I), 1.0, atol=2e-6)
+    fwd.close()
+
+
+def test_graph_replay_equals_step():
+    T = _gpu()
+    prob = W.config_small(steps=20)
+    a = T.Forward(prob)
+    a.step(20)
+    b = T.Forward(prob)
+    b.run(20)
+    b.sync()
+    np.testing.assert_array_equal(a.field(T.FIELD_I), b.field(T.FIELD_I))
+    np.testing.assert_allclose(a.detectors(), b.detectors(), rtol=1e-12, atol=0)
+    b.reset()
+    b.run(20)
+    b.sync()
+    np.testing.assert_array_equal(a.field(T.FIELD_S), b.field(T.FIELD_S))
+    a.close()
+    b.close()
+
+
+def test_invalid_inputs_are_errors():
+    T = _gpu()
+    prob = W.config_small(steps=5)
+    fwd = T.Forward(prob)
+    bad = prob["nidx"].copy()
+    bad[0, 0, 0] = 0.5
+    assert fwd.set_optics(prob["mua"], prob["mus"], bad, 0.9) == -1
+    bad[0, 0, 0] = 3.0  # delay beyond the stored history
+    assert fwd.set_optics(prob["mua"], prob["mus"], bad, 0.9) == -1
+    neg = prob["mua"].copy()
+    neg[1, 1, 1] = -1.0
+    assert fwd.set_optics(neg, prob["mus"], prob["nidx"], 0.9) == -1
+    fwd.close()
+    per = W.homogeneous(4, 4, 4, 2, 0.0, 1.0, boundary="periodic")
+    per["source"] = dict(face=4, u_mm=2, v_mm=2, half_angle_deg=15.0, pulse_steps=1, energy=1.0)
+    with pytest.raises(T.TrinityError):
+        T.Forward(per)
+
+
+def test_device_pointer_optics_and_stream():
+    torch = pytest.importorskip("torch")
+    T = _gpu()
+    prob = W.config_small(steps=10)
+    a = T.Forward(prob)
+    a.step(10)
+    s = torch.cuda.Stream()
+    b = T.Forward(prob, stream=s.cuda_stream)
+    dev = [torch.from_numpy(prob[k]).cuda().contiguous() for k in ("mua", "mus", "nidx")]
+    assert b.set_optics(*dev, prob["g"]) == 0
+    b.step(10)
+    np.testing.assert_array_equal(a.field(T.FIELD_I), b.field(T.FIELD_I))
+    a.close()
+    b.close()
+
+
+def test_full_size_slab_sampled_one_step():
+    """The 96x96x64, 192-direction slab at full size: after 24 steps, level n of 64
+    sampled voxels (plus the source voxel) is recomputed by the oracle from the GPU's
+    own stored history (one step of Eq. 10 plus the source iteration)."""
+    T = _gpu()
+    from oracle.solver import one_step_at, Model
+    prob = W.config_slab(steps=24)
+    fwd = T.Forward(prob)
+    fwd.step(24)
+    n = 24 - 1  # the level just completed
+    hist = {}
+    for back in range(1, 5):
+        lev = n - back
+        if lev >= 0:
+            hist[lev] = (fwd.field(T.FIELD_I, back), fwd.field(T.FIELD_S, back))
+    I_n = fwd.field(T.FIELD_I, 0)
+    S_n = fwd.field(T.FIELD_S, 0)
+
+    def h(which, lev, d, u):
+        out = np.zeros(np.shape(lev))  # levels before 0 are zero
+        for L, (Ia, Sa) in hist.items():
+            m = lev == L
+            if np.any(m):
+                arr = Ia if which == "I" else Sa
+                out[m] = arr[d[m], u[m]]
+        return out
+
+    s_glob = float(np.abs(hist[n - 1][1]).max())
+    nz, ny, nx = prob["nz"], prob["ny"], prob["nx"]
+    rng = np.random.default_rng(5)
+    # voxels near the source carry the signal at this early time
+    cx, cy = nx // 2, ny // 2
+    vox = [(z * ny + y) * nx + x for z, y, x in zip(rng.integers(0, 12, 64), rng.integers(cy - 8, cy + 8, 64),
+                                                      rng.integers(cx - 8, cx + 8, 64))]
+    vox.append((0 * ny + cy) * nx + cx)
+    vox = np.array(sorted(set(vox)))
+    p = dict(prob)
+    p["tol"] = 1e-10
+    I_ref, S_ref, _ = one_step_at(Model(p), n, h, vox, s_glob)
+    scale = np.abs(I_n).max()
+    assert np.abs(I_n[:, vox] - I_ref).max() <= FP32_TOL * scale
+    assert np.abs(S_n[:, vox] - S_ref).max() <= FP32_TOL * np.abs(S_n).max()
+    det = fwd.detectors()
+    assert np.all(np.isfinite(det)) and np.all(det >= 0)
+    N, esc = fwd.energy()
+    assert np.all(N >= 0) and np.all(esc >= 0)
+    fwd.close()

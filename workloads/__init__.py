@@ -162,3 +162,28 @@ def served_stream(n_requests=2000, seed=4, rate_per_s=1.0):
                         nside=2 if rng.random() < 0.5 else 4,
                         steps=int(rng.integers(500, 1501)), seed=int(rng.integers(1 << 31))))
     return out
+
+
+def developed_history(prob, seed=7, levels=4):
+    """A smooth synthetic field history for timing per-voxel work on the CPU: for each
+    stored level (oldest first) an intensity that is a broad Gaussian glow around the
+    source spot (std 15 mm) times (1 + 0.1 u), u uniform in [-1, 1] per voxel and
+    direction, fading by 0.5% per level, with S = 0.9 I.  Returns (I, S), float32 arrays
+    [levels, N_a, N_v]."""
+    nz, ny, nx = prob["nz"], prob["ny"], prob["nx"]
+    na = 12 * prob["nside"] ** 2
+    src = prob["source"]
+    zz, yy, xx = np.meshgrid(np.arange(nz) + 0.5, np.arange(ny) + 0.5, np.arange(nx) + 0.5,
+                             indexing="ij")
+    c = [0.0, 0.0, 0.0]
+    ax = src["face"] // 2
+    uv = [a for a in range(3) if a != ax]
+    c[uv[0]], c[uv[1]] = src["u_mm"], src["v_mm"]
+    c[ax] = 0.0 if src["face"] % 2 == 0 else (nx, ny, nz)[ax] * prob["h"]
+    r2 = (xx - c[0]) ** 2 + (yy - c[1]) ** 2 + (zz - c[2]) ** 2
+    glow = np.exp(-r2 / (2 * 15.0 ** 2)).ravel()
+    rng = np.random.default_rng(seed)
+    I = np.empty((levels, na, glow.size), dtype=np.float32)
+    for k in range(levels):
+        I[k] = glow[None, :] * (1.0 + 0.1 * rng.uniform(-1, 1, (na, glow.size))) * 0.995 ** k
+    return I, (0.9 * I).astype(np.float32)
