@@ -101,7 +101,8 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    prob = W.config_slab(steps=args.spinup + args.warmup + args.steps)
+    nx, ny, nz = args.grid
+    prob = W.config_slab(steps=args.spinup + args.warmup + args.steps, nx=nx, ny=ny, nz=nz)
     vals = []
     info = None
     for k in range(args.warmup + args.steps):
@@ -175,13 +176,15 @@ class ClockSampler:
 
 
 def workload_config(args):
-    return {"workload": "phantom-scale slab 96x96x64 voxels @1mm, 192 HEALPix dirs (Nside 4), "
+    nx, ny, nz = args.grid
+    return {"workload": "phantom-scale slab %dx%dx%d voxels @1mm, 192 HEALPix dirs (Nside 4), " % (nx, ny, nz) +
                         "mu_a 0.008/mm, mu_s 8/mm, g 0.9, n 1.4, 15-deg delta pulse, 8 detectors, "
                         "10 ps bins",
             "window": "time steps %d..%d of the 1500-step solve" % (
                 args.spinup + args.warmup, args.spinup + args.warmup + args.steps - 1),
             "tol": 1e-6, "l2": "inputs larger than L2 (4.5 GB time-level history per solve)",
-            "parallelism": "replicas" if dist_env()[0] > 1 else "single GPU"}
+            "parallelism": "replicas" if dist_env()[0] > 1 else "single GPU",
+            "precision": args.precision}
 
 
 def main():
@@ -199,6 +202,8 @@ def main():
     ap.add_argument("--ref-voxels", type=int, default=2048,
                     help="voxels per bench step of --impl reference")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--grid", type=int, nargs=3, default=[96, 96, 64], metavar=("NX", "NY", "NZ"),
+                    help="slab size (smaller grids are for profiling captures only)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -214,7 +219,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     total = args.spinup + args.warmup + args.steps + 16
-    prob = W.config_slab(steps=total, precision=args.precision)
+    nx, ny, nz = args.grid
+    prob = W.config_slab(steps=total, precision=args.precision, nx=nx, ny=ny, nz=nz)
     stream = torch.cuda.Stream()
     nv = prob["nx"] * prob["ny"] * prob["nz"]
     na = 12 * prob["nside"] ** 2
@@ -309,7 +315,7 @@ def main():
                     "d2h_bytes_per_step": (det.size * 8 + N.size * 16) / job_steps}}
 
     if args.compare_fp32 and args.precision != "fp32":
-        p32 = W.config_slab(steps=total, precision="fp32")
+        p32 = W.config_slab(steps=total, precision="fp32", nx=nx, ny=ny, nz=nz)
         f32 = T.Forward(p32, stream=stream.cuda_stream)
         f32.run(args.spinup + args.warmup)
         f32.sync()

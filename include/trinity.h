@@ -125,8 +125,9 @@ int trinity_set_initial_state(trinity_ctx* ctx, const float* I0, const float* S0
  * I and S, linear in time between stored levels), the per-voxel source iteration
  * S = a P (Q + b1 S) of Eq. 12 started from S(n-1) and stopped when
  *   rho/(1-rho) |S^k - S^(k-1)|_inf <= tol * max(|S^k|_inf, 1e-6 * max|S(n-1)|)
- * (rho = a * max_d b1, a bound on the contraction) or when the change falls to the
- * arithmetic's own resolution, then the detector and energy tallies.  iters_out (may be
+ * (rho = a * max_d b1, a bound on the contraction) or when the change has not reached a
+ * new minimum for three iterations (the iterate sits at the noise floor of the
+ * arithmetic), then the detector and energy tallies.  iters_out (may be
  * NULL) receives the largest iteration count of each step.  Returns
  * TRINITY_W_NOT_CONVERGED if any voxel hit max_iters. */
 int trinity_step(trinity_ctx* ctx, int nsteps, int* iters_out);
@@ -166,6 +167,12 @@ int trinity_reset(trinity_ctx* ctx);
 
 const char* trinity_last_error(const trinity_ctx* ctx);
 void trinity_destroy(trinity_ctx* ctx);
+
+/* Self-test of the tensor-core tile used by TRINITY_BF16: D = A B^T for one 128 x na tile
+ * (na = 48 or 192) with A [128][K] and B [na][K] bf16 (row-major, K = na rounded up to a
+ * multiple of 64, padding zero) and D [128][na] float32; host pointers.  Same operand
+ * layouts, descriptors and TMEM read-out as the iteration kernel.  For testing. */
+int trinity_tc_selftest(int na, const uint16_t* A, const uint16_t* B, float* D);
 
 /* ---- Host-side tables (no GPU needed): the same FP64 tables the context builds. ---- */
 

@@ -48,6 +48,7 @@ SIGNATURES = {
     "trinity_reset": (c_int, [c_void_p]),
     "trinity_last_error": (ctypes.c_char_p, [c_void_p]),
     "trinity_destroy": (None, [c_void_p]),
+    "trinity_tc_selftest": (c_int, [c_int, c_void_p, c_void_p, c_void_p]),
     "trinity_healpix_dirs": (c_int, [c_int, P_double, c_size_t]),
     "trinity_phase_matrix": (c_int, [c_int, c_double, P_double, c_size_t, P_double]),
     "trinity_lattice_tables": (c_int, [c_int, c_int, c_int, c_int, c_double, c_int,

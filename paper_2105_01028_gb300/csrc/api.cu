@@ -16,14 +16,6 @@
 
 using namespace trinity;
 
-namespace trinity {
-cudaError_t launch_scatter_bf16(const GridParams& g, const DirInfo* dirs, const uint16_t* Pbf,
-                                const float* Q, const float* mut, const float* alb,
-                                const float* nidx, float* Iring, float* Sring, float tol,
-                                int max_iters, RunState rs, cudaStream_t st);
-bool scatter_bf16_supported(int na);
-}  // namespace trinity
-
 struct trinity_ctx {
   trinity_grid_desc desc{};
   cudaStream_t stream = nullptr;
@@ -52,7 +44,8 @@ struct trinity_ctx {
 
   // device buffers
   float *I = nullptr, *S = nullptr, *Q = nullptr;
-  float *mut = nullptr, *alb = nullptr, *nidx = nullptr;
+  float *mut = nullptr, *eps = nullptr, *nidx = nullptr;
+  float* d_rcorr32 = nullptr;
   float* P32 = nullptr;
   uint16_t* Pbf = nullptr;
   DirInfo* d_dirs = nullptr;
@@ -66,6 +59,11 @@ struct trinity_ctx {
   unsigned* d_smax = nullptr;
   int* d_nonconv = nullptr;
   int* d_error = nullptr;
+  int* d_tile_ctr = nullptr;
+  float* d_rcorr = nullptr;
+  uint8_t* d_cls = nullptr;
+  float* d_cls_ds = nullptr;
+  int ncls = 0;
   int* d_iters_max = nullptr;
   unsigned long long* d_iters_sum = nullptr;
   double* d_energy = nullptr;
@@ -161,6 +159,7 @@ RunState run_state(trinity_ctx* c) {
   rs.nonconv = c->d_nonconv;
   rs.bins = c->d_bins;
   rs.error = c->d_error;
+  rs.tile_ctr = c->d_tile_ctr;
   return rs;
 }
 
@@ -252,6 +251,15 @@ int lock_inputs(trinity_ctx* ctx) {
   return TRINITY_OK;
 }
 
+BfTables bf_tables(trinity_ctx* c) {
+  BfTables t;
+  t.rcorr = c->d_rcorr;
+  t.cls = c->d_cls;
+  t.cls_ds = c->d_cls_ds;
+  t.ncls = c->ncls;
+  return t;
+}
+
 // The launches of one time step (all on ctx->stream; the step index lives on the device).
 int enqueue_step(trinity_ctx* ctx) {
   const RunState rs = run_state(ctx);
@@ -259,11 +267,11 @@ int enqueue_step(trinity_ctx* ctx) {
   CK(launch_sweep(g, ctx->d_dirs, ctx->d_offs, ctx->I, ctx->S, ctx->mut, ctx->nidx, ctx->Q, rs,
                   ctx->stream));
   if (ctx->desc.precision == TRINITY_BF16) {
-    CK(launch_scatter_bf16(g, ctx->d_dirs, ctx->Pbf, ctx->Q, ctx->mut, ctx->alb, ctx->nidx, ctx->I,
+    CK(launch_scatter_bf16(g, bf_tables(ctx), ctx->Pbf, ctx->Q, ctx->mut, ctx->eps, ctx->nidx, ctx->I,
                            ctx->S, static_cast<float>(ctx->desc.tol), ctx->desc.max_iters, rs,
                            ctx->stream));
   } else {
-    CK(launch_scatter_fp32(g, ctx->d_dirs, ctx->P32, ctx->Q, ctx->mut, ctx->alb, ctx->nidx, ctx->I,
+    CK(launch_scatter_fp32(g, ctx->d_dirs, ctx->P32, ctx->d_rcorr32, ctx->Q, ctx->mut, ctx->eps, ctx->nidx, ctx->I,
                            ctx->S, static_cast<float>(ctx->desc.tol), ctx->desc.max_iters, rs,
                            ctx->stream));
   }
@@ -357,7 +365,9 @@ int trinity_create_grid(const trinity_grid_desc* desc, void* cuda_stream, trinit
     di.a0 = ax[0];
     di.a1 = ax[1];
     di.ds = static_cast<float>(ctx->lat.ds[d]);
-    di.dcoef = static_cast<float>(ctx->lat.ds[d] / (kC0 * ctx->dt));
+    const double dc = ctx->lat.ds[d] / (kC0 * ctx->dt);
+    di.dcoef = static_cast<float>(dc);
+    di.dcoef_lo = static_cast<float>(dc - static_cast<double>(di.dcoef));
     dsmax = std::max(dsmax, ctx->lat.ds[d]);
     for (int f = 0; f < 6; ++f) {
       const double c = ((f % 2) ? 1.0 : -1.0) * ctx->dirs[3 * d + f / 2];
@@ -369,18 +379,39 @@ int trinity_create_grid(const trinity_grid_desc* desc, void* cuda_stream, trinit
   const size_t nv = g.nv, na = g.na;
   if (dalloc(&ctx->I, kRing * na * nv) != cudaSuccess || dalloc(&ctx->S, kRing * na * nv) != cudaSuccess ||
       dalloc(&ctx->Q, na * nv) != cudaSuccess || dalloc(&ctx->mut, nv) != cudaSuccess ||
-      dalloc(&ctx->alb, nv) != cudaSuccess || dalloc(&ctx->nidx, nv) != cudaSuccess ||
+      dalloc(&ctx->eps, nv) != cudaSuccess || dalloc(&ctx->nidx, nv) != cudaSuccess ||
       dalloc(&ctx->P32, na * na) != cudaSuccess || dalloc(&ctx->Pbf, na * na) != cudaSuccess ||
       dalloc(&ctx->d_dirs, na) != cudaSuccess ||
       dalloc(&ctx->d_offs, ctx->lat.off.size()) != cudaSuccess || dalloc(&ctx->d_step, 1) != cudaSuccess ||
       dalloc(&ctx->d_smax, 2) != cudaSuccess || dalloc(&ctx->d_nonconv, 1) != cudaSuccess ||
-      dalloc(&ctx->d_error, 1) != cudaSuccess) {
+      dalloc(&ctx->d_error, 1) != cudaSuccess || dalloc(&ctx->d_tile_ctr, 2) != cudaSuccess ||
+      dalloc(&ctx->d_rcorr, na) != cudaSuccess || dalloc(&ctx->d_rcorr32, na) != cudaSuccess ||
+      dalloc(&ctx->d_cls, na) != cudaSuccess ||
+      dalloc(&ctx->d_cls_ds, 16) != cudaSuccess) {
     cudaGetLastError();
     return bail(TRINITY_E_OOM);
   }
   if (cudaMemcpy(ctx->d_offs, ctx->lat.off.data(), ctx->lat.off.size(), cudaMemcpyHostToDevice) !=
       cudaSuccess)
     return bail(TRINITY_E_CUDA);
+  {
+    // classes of equal ray-sample spacing (the tensor-core kernel tabulates b1 per class)
+    std::vector<uint8_t> cls(g.na);
+    std::vector<float> cds;
+    for (int d = 0; d < g.na; ++d) {
+      const float ds = static_cast<float>(ctx->lat.ds[d]);
+      int k = 0;
+      while (k < static_cast<int>(cds.size()) && cds[k] != ds) ++k;
+      if (k == static_cast<int>(cds.size())) cds.push_back(ds);
+      cls[d] = static_cast<uint8_t>(k < 255 ? k : 255);
+    }
+    ctx->ncls = static_cast<int>(cds.size());
+    if (desc->precision == TRINITY_BF16 && ctx->ncls > 16) return bail(TRINITY_E_UNSUPPORTED);
+    cds.resize(16, 0.0f);
+    if (cudaMemcpy(ctx->d_cls, cls.data(), g.na, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ctx->d_cls_ds, cds.data(), 16 * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(TRINITY_E_CUDA);
+  }
   if (trinity_reset(ctx) != TRINITY_OK) return bail(TRINITY_E_CUDA);
   *out = ctx;
   return TRINITY_OK;
@@ -408,7 +439,7 @@ int trinity_set_optics(trinity_ctx* ctx, const float* mua, const float* mus, con
     dsmin = std::min(dsmin, ds);
     dsmax = std::max(dsmax, ds);
   }
-  std::vector<float> mt(nv), al(nv);
+  std::vector<float> mt(nv), al(nv);  // al: eps = mu_a / mu_t (1 where mu_t = 0)
   for (size_t v = 0; v < nv; ++v) {
     if (!(a[v] >= 0.0f) || !(s[v] >= 0.0f) || !std::isfinite(a[v]) || !std::isfinite(s[v]) ||
         !(r[v] >= 1.0f) || !std::isfinite(r[v]))
@@ -416,7 +447,8 @@ int trinity_set_optics(trinity_ctx* ctx, const float* mua, const float* mus, con
     nmin = std::min(nmin, double(r[v]));
     nmax = std::max(nmax, double(r[v]));
     mt[v] = a[v] + s[v];
-    al[v] = mt[v] > 0.0f ? s[v] / mt[v] : 0.0f;
+    const double t64 = static_cast<double>(a[v]) + static_cast<double>(s[v]);
+    al[v] = t64 > 0.0 ? static_cast<float>(static_cast<double>(a[v]) / t64) : 1.0f;
   }
   const double dlo = dsmin * nmin / (kC0 * ctx->dt), dhi = dsmax * nmax / (kC0 * ctx->dt);
   if (dlo < 1.0 || dhi >= kRing - 1)
@@ -434,8 +466,29 @@ int trinity_set_optics(trinity_ctx* ctx, const float* mua, const float* mus, con
     P32[k] = static_cast<float>(P[k]);
     Pb[k] = to_bf16(P32[k]);
   }
+  // diagonal correction that gives bf16(P) + diag(r) unit row and column sums
+  const int na = ctx->g.na;
+  std::vector<float> rc(na);
+  for (int i = 0; i < na; ++i) {
+    double rs = 0.0;
+    for (int j = 0; j < na; ++j) {
+      const uint32_t u = static_cast<uint32_t>(Pb[static_cast<size_t>(i) * na + j]) << 16;
+      float f;
+      std::memcpy(&f, &u, 4);
+      rs += f;
+    }
+    rc[i] = static_cast<float>(1.0 - rs);
+  }
+  CK(cudaMemcpy(ctx->d_rcorr, rc.data(), na * sizeof(float), cudaMemcpyHostToDevice));
+  // the same correction for the FP32 matrix of the plain mode
+  for (int i = 0; i < na; ++i) {
+    double rs = 0.0;
+    for (int j = 0; j < na; ++j) rs += P32[static_cast<size_t>(i) * na + j];
+    rc[i] = static_cast<float>(1.0 - rs);
+  }
+  CK(cudaMemcpy(ctx->d_rcorr32, rc.data(), na * sizeof(float), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->mut, mt.data(), nv * 4, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(ctx->alb, al.data(), nv * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->eps, al.data(), nv * 4, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->nidx, r.data(), nv * 4, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->P32, P32.data(), P32.size() * 4, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->Pbf, Pb.data(), Pb.size() * 2, cudaMemcpyHostToDevice));
@@ -668,11 +721,11 @@ int trinity_profile_steps(trinity_ctx* ctx, int nsteps, double* kernel_ms) {
                     ctx->stream));
     CK(cudaEventRecord(e[1], ctx->stream));
     if (ctx->desc.precision == TRINITY_BF16)
-      CK(launch_scatter_bf16(g, ctx->d_dirs, ctx->Pbf, ctx->Q, ctx->mut, ctx->alb, ctx->nidx, ctx->I,
+      CK(launch_scatter_bf16(g, bf_tables(ctx), ctx->Pbf, ctx->Q, ctx->mut, ctx->eps, ctx->nidx, ctx->I,
                              ctx->S, static_cast<float>(ctx->desc.tol), ctx->desc.max_iters, rs,
                              ctx->stream));
     else
-      CK(launch_scatter_fp32(g, ctx->d_dirs, ctx->P32, ctx->Q, ctx->mut, ctx->alb, ctx->nidx, ctx->I,
+      CK(launch_scatter_fp32(g, ctx->d_dirs, ctx->P32, ctx->d_rcorr32, ctx->Q, ctx->mut, ctx->eps, ctx->nidx, ctx->I,
                              ctx->S, static_cast<float>(ctx->desc.tol), ctx->desc.max_iters, rs,
                              ctx->stream));
     CK(cudaEventRecord(e[2], ctx->stream));
@@ -788,6 +841,7 @@ int trinity_reset(trinity_ctx* ctx) {
   CK(cudaMemset(ctx->d_smax, 0, 2 * sizeof(unsigned)));
   CK(cudaMemset(ctx->d_nonconv, 0, sizeof(int)));
   CK(cudaMemset(ctx->d_error, 0, sizeof(int)));
+  CK(cudaMemset(ctx->d_tile_ctr, 0, 2 * sizeof(int)));
   if (ctx->capacity > 0) {
     CK(cudaMemset(ctx->d_iters_max, 0, ctx->capacity * sizeof(int)));
     CK(cudaMemset(ctx->d_iters_sum, 0, ctx->capacity * sizeof(unsigned long long)));
@@ -814,14 +868,49 @@ const char* trinity_last_error(const trinity_ctx* ctx) {
 void trinity_destroy(trinity_ctx* ctx) {
   if (!ctx) return;
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
-  void* bufs[] = {ctx->I,         ctx->S,          ctx->Q,           ctx->mut,       ctx->alb,
+  void* bufs[] = {ctx->I,         ctx->S,          ctx->Q,           ctx->mut,       ctx->eps,
                   ctx->nidx,      ctx->P32,        ctx->Pbf,         ctx->d_dirs,    ctx->d_offs,
                   ctx->d_det_vox, ctx->d_det_dir,  ctx->d_det_id,    ctx->d_det_w,   ctx->d_det,
                   ctx->d_step,    ctx->d_smax,     ctx->d_nonconv,   ctx->d_error,   ctx->d_iters_max,
-                  ctx->d_iters_sum, ctx->d_energy, ctx->d_escaped,   ctx->d_bins};
+                  ctx->d_iters_sum, ctx->d_energy, ctx->d_escaped,   ctx->d_bins,
+                  ctx->d_tile_ctr, ctx->d_rcorr,   ctx->d_cls,       ctx->d_cls_ds,
+                  ctx->d_rcorr32};
   for (void* p : bufs)
     if (p) cudaFree(p);
   delete ctx;
+}
+
+int trinity_tc_selftest(int na, const uint16_t* A, const uint16_t* B, float* D) {
+  if (!A || !B || !D || (na != 48 && na != 192)) return TRINITY_E_INVALID;
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+    return TRINITY_E_CUDA;
+  if (!(prop.major == 10 && prop.minor == 3)) return TRINITY_E_UNSUPPORTED;
+  const int kp = (na + 63) / 64 * 64;
+  uint16_t *dA = nullptr, *dB = nullptr;
+  float* dD = nullptr;
+  int* dErr = nullptr;
+  int rc = TRINITY_OK;
+  if (cudaMalloc(&dA, 128 * kp * 2) != cudaSuccess || cudaMalloc(&dB, na * kp * 2) != cudaSuccess ||
+      cudaMalloc(&dD, 128 * na * 4) != cudaSuccess || cudaMalloc(&dErr, 4) != cudaSuccess) {
+    rc = TRINITY_E_OOM;
+  } else if (cudaMemcpy(dA, A, 128 * kp * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(dB, B, na * kp * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemset(dErr, 0, 4) != cudaSuccess || tc_tile_selftest(na, dA, dB, dD, dErr, 0) != cudaSuccess ||
+             cudaDeviceSynchronize() != cudaSuccess ||
+             cudaMemcpy(D, dD, 128 * na * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    rc = TRINITY_E_CUDA;
+  } else {
+    int e = 0;
+    if (cudaMemcpy(&e, dErr, 4, cudaMemcpyDeviceToHost) != cudaSuccess) rc = TRINITY_E_CUDA;
+    else if (e != 0) rc = TRINITY_E_TIMEOUT;
+  }
+  cudaFree(dA);
+  cudaFree(dB);
+  cudaFree(dD);
+  cudaFree(dErr);
+  return rc;
 }
 
 // ---- host-side tables ----

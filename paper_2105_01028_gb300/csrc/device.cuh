@@ -12,7 +12,8 @@ struct DirInfo {
   int sgn;        // travel sign along dom
   int a0, a1;     // transverse axes (increasing order)
   float ds;       // ray-sample spacing h / |Omega_dom| (mm)
-  float dcoef;    // ds / (c0 dt): retarded delay in steps per unit refractive index
+  float dcoef;    // ds / (c0 dt): retarded delay in steps per unit refractive index (hi part)
+  float dcoef_lo; // ds / (c0 dt) - dcoef (lo part: the delay's fraction is exact to FP32)
   float src_amp;  // inflow intensity while the pulse is on (0: not a source direction)
   float wcos_out[6];  // w * (Omega . n_out) * h^2 * dt for faces the ray leaves (else 0)
 };
@@ -42,9 +43,39 @@ struct RunState {
   int* nonconv;                  // count of voxel-steps that hit max_iters
   int* bins;                     // [capacity] detector bin of each step (-1: none)
   int* error;                    // device error word (0 = ok)
+  int* tile_ctr;                 // [2] work counters of the persistent kernels (ping-pong)
+};
+
+// Tables of the tensor-core source iteration.
+struct BfTables {
+  const float* rcorr;    // [na] 1 - row sum of bf16(P): diagonal correction (FP32)
+  const uint8_t* cls;    // [na] class of each direction's sample spacing ds
+  const float* cls_ds;   // [ncls] ds of each class
+  int ncls;              // <= 16
 };
 
 __host__ __device__ inline int ring_slot(int level) { return ((level % 5) + 5) % 5; }
+
+// Retarded delay delta = ds n / (c0 dt) split as m + f (m = floor(delta), 0 <= f < 1).
+// dcoef is carried as hi + lo floats and the product with n is formed with its exact
+// FMA error term, so f is accurate to FP32 rounding of f itself (a plain FP32 product
+// would carry an absolute error of ~2e-7 into the time-interpolation weights).
+__device__ __forceinline__ void retarded_delay(float dc_hi, float dc_lo, float n, int& m, float& f) {
+  const float p = n * dc_hi;
+  const float e = fmaf(n, dc_hi, -p);
+  const float lo = fmaf(n, dc_lo, e);
+  const float fl = floorf(p);
+  float fr = (p - fl) + lo;
+  m = static_cast<int>(fl);
+  if (fr < 0.0f) {
+    fr += 1.0f;
+    m -= 1;
+  } else if (fr >= 1.0f) {
+    fr -= 1.0f;
+    m += 1;
+  }
+  f = fr;
+}
 
 // exp(-x), b0(x), b1(x) of Eq. 9: b0 = [1 - (1+x) e^-x]/x, b1 = [x - 1 + e^-x]/x.
 // For x < 1 the closed forms cancel catastrophically in FP32, so their Taylor series
@@ -90,7 +121,8 @@ cudaError_t launch_sweep(const GridParams& g, const DirInfo* dirs, const int8_t*
                          const float* Iring, const float* Sring, const float* mut,
                          const float* nidx, float* Q, RunState rs, cudaStream_t st);
 cudaError_t launch_scatter_fp32(const GridParams& g, const DirInfo* dirs, const float* P,
-                                const float* Q, const float* mut, const float* alb,
+                                const float* rcorr, const float* Q, const float* mut,
+                                const float* eps,
                                 const float* nidx, float* Iring, float* Sring, float tol,
                                 int max_iters, RunState rs, cudaStream_t st);
 cudaError_t launch_tally(const GridParams& g, const DirInfo* dirs, const float* Iring,
@@ -98,5 +130,12 @@ cudaError_t launch_tally(const GridParams& g, const DirInfo* dirs, const float* 
                          const int* det_id, int n_det_entries, double* det, int nbins,
                          RunState rs, cudaStream_t st);
 cudaError_t launch_advance(RunState rs, cudaStream_t st);
+bool scatter_bf16_supported(int na);
+cudaError_t launch_scatter_bf16(const GridParams& g, const BfTables& t, const uint16_t* Pbf,
+                                const float* Q, const float* mut, const float* eps,
+                                const float* nidx, float* Iring, float* Sring, float tol,
+                                int max_iters, RunState rs, cudaStream_t st);
+cudaError_t tc_tile_selftest(int na, const uint16_t* A, const uint16_t* B, float* D, int* err,
+                             cudaStream_t st);
 
 }  // namespace trinity

@@ -32,7 +32,10 @@ __global__ void __launch_bounds__(256) sweep_kernel(GridParams g, const DirInfo*
                                                     float* __restrict__ Q, RunState rs) {
   const int n = *rs.step;
   const int d = blockIdx.y;
-  if (d == 0 && blockIdx.x == 0 && threadIdx.x == 0) rs.smax[n & 1] = 0u;
+  if (d == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+    rs.smax[n & 1] = 0u;      // max |S(n)|, filled by this step's source iteration
+    rs.tile_ctr[n & 1] = 0;   // work counter of this step's persistent kernel
+  }
   const DirInfo di = dirs[d];
   const size_t plane = static_cast<size_t>(g.nv);
   const int8_t* off0 = offs + (static_cast<size_t>(d) * 2 + 0) * g.nmax;
@@ -66,9 +69,9 @@ __global__ void __launch_bounds__(256) sweep_kernel(GridParams g, const DirInfo*
     } else if (q0 < 0 || q0 >= n0 || q1 < 0 || q1 >= n1) {
       kind = 2;
     }
-    const float delta = di.dcoef * nidx[v];
-    const int m = static_cast<int>(floorf(delta));
-    const float f = delta - static_cast<float>(m);
+    int m;
+    float f;
+    retarded_delay(di.dcoef, di.dcoef_lo, nidx[v], m, f);
     const int L0 = n - m, L1 = n - m - 1;
     float Iup = 0.0f, Sup = 0.0f;
     if (kind == 0) {
@@ -101,8 +104,11 @@ __global__ void __launch_bounds__(256) sweep_kernel(GridParams g, const DirInfo*
 // ----------------------------------------------------------------------------------------
 // Source iteration on CUDA cores (plain FP32 mode).
 // A CTA owns a tile of 32 voxels; thread i < NA owns outgoing direction i of all 32.
-// Per iteration: Y[v][i] = sum_j P[i][j] X[v][j] (P symmetric, read as P[j][i] so a warp
-// reads a contiguous row), S_new = a Y, X = Q + b1 S.  The per-voxel stop test needs the
+// Per iteration: Y[v][i] = sum_j P[i][j] X[v][j] + r_i X[v][i] (P symmetric, read as
+// P[j][i] so a warp reads a contiguous row; r_i = 1 - sum_j P[i][j] restores the unit row
+// and column sums that FP32 rounding of P breaks), S_new = (1 - eps) Y with
+// eps = mu_a / mu_t (albedo a = 1 - eps: forming a itself in FP32 would misstate the
+// small absorption 1 - a by up to 6e-5 relative), X = Q + b1 S.  The per-voxel stop test needs the
 // max over directions of |S_new - S_old| and |S_new|: a warp "transpose" reduction leaves
 // lane v holding the warp's maximum for voxel v, then the warps combine through smem.
 // ----------------------------------------------------------------------------------------
@@ -134,16 +140,17 @@ __device__ __forceinline__ float warp_transpose_max(float (&vals)[32], int lane)
 template <int NA>
 __global__ void __launch_bounds__(ScatterCfg<NA>::kThreads)
     scatter_fp32_kernel(GridParams g, const DirInfo* __restrict__ dirs, const float* __restrict__ P,
-                        const float* __restrict__ Q, const float* __restrict__ mut,
-                        const float* __restrict__ alb, const float* __restrict__ nidx,
+                        const float* __restrict__ rcorr, const float* __restrict__ Q,
+                        const float* __restrict__ mut, const float* __restrict__ eps,
+                        const float* __restrict__ nidx,
                         float* __restrict__ Iring, float* __restrict__ Sring, float tol,
                         int max_iters, RunState rs) {
   constexpr int W = ScatterCfg<NA>::kWarps;
   __shared__ __align__(16) float Xs[2][NA][kXStride];
   __shared__ float red_d[W][kTile];
   __shared__ float red_s[W][kTile];
-  __shared__ float a_s[kTile], rho_s[kTile];
-  __shared__ int iters_s[kTile];
+  __shared__ float e_s[kTile], rho_s[kTile], best_s[kTile];
+  __shared__ int iters_s[kTile], stall_s[kTile];
   __shared__ unsigned act_s;
 
   const int n = *rs.step;
@@ -157,21 +164,24 @@ __global__ void __launch_bounds__(ScatterCfg<NA>::kThreads)
 
   if (tid < kTile) {
     const int v = v0 + tid;
-    float a = 0.0f, rho = 0.0f;
+    float ev = 1.0f, rho = 0.0f;
     if (v < g.nv) {
-      a = alb[v];
+      ev = eps[v];
       const float xm = mut[v] * g.ds_max;
-      rho = a * ray_b1(xm, expf(-xm));  // b1 grows with x: max over d is at ds_max
+      rho = (1.0f - ev) * ray_b1(xm, expf(-xm));  // b1 grows with x: max over d is at ds_max
     }
-    a_s[tid] = a;
+    e_s[tid] = ev;
     rho_s[tid] = rho;
     iters_s[tid] = 0;
+    best_s[tid] = 3.0e38f;
+    stall_s[tid] = 0;
   }
   if (tid == 0) act_s = (g.nv - v0 >= kTile) ? 0xffffffffu : ((1u << (g.nv - v0)) - 1u);
   __syncthreads();
 
   float q[kTile], b1[kTile], so[kTile], acc[kTile];
   const float ds = live ? dirs[i].ds : 0.0f;
+  const float ri = live ? rcorr[i] : 0.0f;
   const bool has_prev = (n - 1) >= g.hist_from;
   const size_t prev_off = (static_cast<size_t>(ring_slot(n - 1)) * g.na + (live ? i : 0)) * plane;
 #pragma unroll
@@ -220,7 +230,8 @@ __global__ void __launch_bounds__(ScatterCfg<NA>::kThreads)
 #pragma unroll
     for (int v = 0; v < kTile; ++v) {
       const bool on = live && ((act >> v) & 1u);
-      const float sn = a_s[v] * acc[v];
+      const float y = fmaf(ri, fmaf(b1[v], so[v], q[v]), acc[v]);  // + r_i X_i
+      const float sn = fmaf(-e_s[v], y, y);                        // (1 - eps) y
       dsv[v] = on ? fabsf(sn - so[v]) : 0.0f;
       smv[v] = on ? fabsf(sn) : 0.0f;
       so[v] = on ? sn : so[v];
@@ -249,8 +260,17 @@ __global__ void __launch_bounds__(ScatterCfg<NA>::kThreads)
         }
         const float r = rho_s[v];
         const float scale = fmaxf(Sm, 1e-6f * s_glob);
-        // stop: error bound within tol, or the change is at FP32 resolution (~4 ulp)
-        const bool stop = (r / (1.0f - r)) * D <= tol * scale || D <= 2.384185791e-7f * Sm;
+        if (D < best_s[v]) {
+          best_s[v] = D;
+          stall_s[v] = 0;
+        } else {
+          stall_s[v] += 1;
+        }
+        // stop: the error bound is within tol, or the change has stopped shrinking for
+        // three iterations (the iterate has reached the noise floor of FP32 arithmetic and
+        // fluctuates around the fixed point; a fixed floor on the change would instead stop
+        // on one side of it every step and bias the result)
+        const bool stop = (r / (1.0f - r)) * D <= tol * scale || stall_s[v] >= 3;
         if (stop) {
           done = 1u;
           iters_s[v] = k;
@@ -392,22 +412,22 @@ cudaError_t launch_sweep(const GridParams& g, const DirInfo* dirs, const int8_t*
 }
 
 cudaError_t launch_scatter_fp32(const GridParams& g, const DirInfo* dirs, const float* P,
-                                const float* Q, const float* mut, const float* alb,
-                                const float* nidx, float* Iring, float* Sring, float tol,
-                                int max_iters, RunState rs, cudaStream_t st) {
+                                const float* rcorr, const float* Q, const float* mut,
+                                const float* eps, const float* nidx, float* Iring, float* Sring,
+                                float tol, int max_iters, RunState rs, cudaStream_t st) {
   const int tiles = (g.nv + kTile - 1) / kTile;
   switch (g.na) {
     case 12:
       scatter_fp32_kernel<12><<<tiles, ScatterCfg<12>::kThreads, 0, st>>>(
-          g, dirs, P, Q, mut, alb, nidx, Iring, Sring, tol, max_iters, rs);
+          g, dirs, P, rcorr, Q, mut, eps, nidx, Iring, Sring, tol, max_iters, rs);
       break;
     case 48:
       scatter_fp32_kernel<48><<<tiles, ScatterCfg<48>::kThreads, 0, st>>>(
-          g, dirs, P, Q, mut, alb, nidx, Iring, Sring, tol, max_iters, rs);
+          g, dirs, P, rcorr, Q, mut, eps, nidx, Iring, Sring, tol, max_iters, rs);
       break;
     case 192:
       scatter_fp32_kernel<192><<<tiles, ScatterCfg<192>::kThreads, 0, st>>>(
-          g, dirs, P, Q, mut, alb, nidx, Iring, Sring, tol, max_iters, rs);
+          g, dirs, P, rcorr, Q, mut, eps, nidx, Iring, Sring, tol, max_iters, rs);
       break;
     default:
       return cudaErrorInvalidValue;

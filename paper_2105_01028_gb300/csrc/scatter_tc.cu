@@ -1,17 +1,700 @@
-// Source iteration with the angular sum of Eq. 12 on the tcgen05 tensor cores (BF16 in,
-// FP32 accumulate in tensor memory).
+// Source iteration with the angular sum of Eq. 12 on the 5th-generation tensor cores
+// (tcgen05): BF16 operands, FP32 accumulation in tensor memory (TMEM).
+//
+// Per voxel the iteration is S <- a P (Q + b1 o S) (Eq. 12 with Eq. 10).  A CTA owns a
+// tile of 128 voxels (the MMA's M) and loops over tiles (persistent, one CTA per SM,
+// tiles handed out by an atomic counter).  Per iteration:
+//   D[v][i]  = sum_j X_hi[v][j] Pb[i][j] + sum_j X_lo[v][j] Pb[i][j]   (two MMA chains)
+//   Y        = D + r o X                   (FP32 diagonal correction, see below)
+//   S_new    = (1 - eps) Y,   X_new = Q + b1 o S_new,   X_new -> (X_hi, X_lo) in BF16
+// (eps = mu_a / mu_t, the albedo a = 1 - eps is never rounded to FP32 on its own)
+// X is carried as two BF16 terms (hi = bf16(X), lo = bf16(X - hi)), so the product is
+// FP32-grade: a single BF16 term carries 2^-9 rounding noise that the slow contraction
+// (rho ~ 0.92) amplifies about tenfold, far above the 1e-3 target on detector curves.
+// Pb = bf16(P) is symmetric; r_i = 1 - sum_j Pb[i][j] restores unit row and column sums
+// exactly (Pb + diag(r) is symmetric and doubly stochastic), so scattering still
+// conserves photons and keeps isotropic fields isotropic.
+//
+// Operand layouts (shared memory, K-major, 128-byte swizzle): a K-block of 64 BF16 per
+// row is 128 B; rows follow each other every 128 B, 8-row groups every 1024 B; the
+// 16-byte chunk c of row r sits at chunk position c ^ (r & 7).  A = X tile (128 rows x
+// K), B = Pb (N_a rows x K), K padded to a multiple of 64 with zeros.
+// TMEM: columns [0, N_a) hold D, columns [SOFF, SOFF + N_a) hold S_old (FP32).
+// Thread mapping: 12 warps; warp w reads TMEM lanes 32 (w % 4) .. + 31 (one voxel row
+// per thread) and the column group w / 4 (a third of the directions).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
 #include <cstdint>
 
 #include "device.cuh"
 
 namespace trinity {
 
-bool scatter_bf16_supported(int na) { (void)na; return false; }
+namespace {
 
-cudaError_t launch_scatter_bf16(const GridParams&, const DirInfo*, const uint16_t*, const float*,
-                                const float*, const float*, const float*, float*, float*, float,
-                                int, RunState, cudaStream_t) {
-  return cudaErrorNotSupported;
+constexpr int kM = 128;
+constexpr int kGroups = 3;                 // column groups (warps w, w+4, w+8 share TMEM lanes)
+constexpr int kThreadsTc = 128 * kGroups;
+constexpr int kMaxClasses = 16;
+constexpr long long kWaitCycles = 2000000000LL;  // ~1 s: bound on every mbarrier wait
+
+template <int NA>
+struct Tc {
+  static constexpr int KP = (NA + 63) / 64 * 64;   // padded K
+  static constexpr int KB = KP / 64;               // 128-byte K blocks
+  static constexpr int KSTEPS = KP / 16;           // MMAs per operand (K = 16 each)
+  static constexpr int HALF = NA / kGroups;        // columns per thread
+  static constexpr int CH = (HALF % 16 == 0) ? 16 : 8;  // TMEM load width
+  static constexpr int NCH = HALF / CH;
+  static_assert(HALF % 8 == 0, "column group must be a whole number of 16-byte chunks");
+  static constexpr int POW2 = NA <= 64 ? 64 : (NA <= 128 ? 128 : 256);
+  static constexpr int TCOLS = 2 * POW2;           // TMEM allocation (power of 2 >= 32)
+  static constexpr int SOFF = POW2;                // S_old column offset
+  static constexpr int B_BYTES = KB * NA * 128;
+  static constexpr int A_BYTES = KB * kM * 128;
+  static constexpr int OFF_B = 0;
+  static constexpr int OFF_AHI = OFF_B + ((B_BYTES + 1023) / 1024) * 1024;
+  static constexpr int OFF_ALO = OFF_AHI + A_BYTES;
+  static constexpr int OFF_B1T = OFF_ALO + A_BYTES;                 // [kMaxClasses][kM] f32
+  static constexpr int OFF_R = OFF_B1T + kMaxClasses * kM * 4;      // [NA] f32
+  static constexpr int OFF_CLS = OFF_R + NA * 4;                    // [NA] u8 (padded)
+  static constexpr int OFF_END = OFF_CLS + ((NA + 15) / 16) * 16;
+  static constexpr int SMEM = OFF_END + 1024;                       // + alignment slack
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
+                                    (static_cast<uint32_t>(NA >> 3) << 17) |
+                                    (static_cast<uint32_t>(kM >> 4) << 24);
+};
+
+// ---------------------------------------------------------------- PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  return static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4) | (static_cast<uint64_t>(1) << 16) |
+         (static_cast<uint64_t>(1024 >> 4) << 32) | (static_cast<uint64_t>(1) << 46) |
+         (static_cast<uint64_t>(2) << 61);
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+
+// Bounded wait; returns false if it ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[N]);
+
+template <>
+__device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <>
+__device__ __forceinline__ void tmem_ld<8>(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int N>
+__device__ __forceinline__ void tmem_st(uint32_t taddr, const float (&v)[N]);
+
+template <>
+__device__ __forceinline__ void tmem_st<16>(uint32_t taddr, const float (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+
+template <>
+__device__ __forceinline__ void tmem_st<8>(uint32_t taddr, const float (&v)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+               "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+               "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+               "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+               : "memory");
+}
+
+// Byte offset of the 16-byte chunk holding K elements [k0, k0+8) of row r in a
+// swizzled K-major operand with ``rows`` rows.
+__device__ __forceinline__ uint32_t sw128_chunk_off(int rows, int r, int k0) {
+  const int kb = k0 >> 6;
+  const int ch = (k0 & 63) >> 3;
+  return static_cast<uint32_t>(kb * rows * 128 + r * 128 + ((ch ^ (r & 7)) << 4));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&b);
+}
+
+__device__ __forceinline__ void split_bf16x2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  hi = pack_bf16x2(x0, x1);
+  const float h0 = __uint_as_float(hi << 16);
+  const float h1 = __uint_as_float(hi & 0xffff0000u);
+  lo = pack_bf16x2(x0 - h0, x1 - h1);
+}
+
+// Issue the two MMA chains of one iteration: D = X_hi Pb^T + X_lo Pb^T.
+template <int NA>
+__device__ __forceinline__ void issue_mmas(uint32_t tmem_d, uint32_t a_hi, uint32_t a_lo, uint32_t b) {
+  using C = Tc<NA>;
+#pragma unroll
+  for (int s = 0; s < C::KSTEPS; ++s) {
+    const uint32_t ko = static_cast<uint32_t>((s & 3) * 32);
+    const uint32_t kb = static_cast<uint32_t>(s >> 2);
+    mma_bf16(tmem_d, sw128_desc(a_hi + kb * kM * 128 + ko), sw128_desc(b + kb * NA * 128 + ko), C::IDESC,
+             s > 0 ? 1u : 0u);
+  }
+#pragma unroll
+  for (int s = 0; s < C::KSTEPS; ++s) {
+    const uint32_t ko = static_cast<uint32_t>((s & 3) * 32);
+    const uint32_t kb = static_cast<uint32_t>(s >> 2);
+    mma_bf16(tmem_d, sw128_desc(a_lo + kb * kM * 128 + ko), sw128_desc(b + kb * NA * 128 + ko), C::IDESC, 1u);
+  }
+}
+
+// Load Pb [NA][NA] (row-major bf16) into the swizzled B operand, zero K padding.
+template <int NA>
+__device__ __forceinline__ void load_b_operand(uint8_t* sB, const uint16_t* __restrict__ Pbf) {
+  using C = Tc<NA>;
+  const int units = NA * C::KB * 8;
+  for (int u = threadIdx.x; u < units; u += blockDim.x) {
+    const int row = u / (C::KB * 8);
+    const int rem = u % (C::KB * 8);
+    const int k0 = (rem / 8) * 64 + (rem % 8) * 8;
+    uint4 val = make_uint4(0u, 0u, 0u, 0u);
+    if (k0 < NA) val = *reinterpret_cast<const uint4*>(Pbf + static_cast<size_t>(row) * NA + k0);
+    *reinterpret_cast<uint4*>(sB + sw128_chunk_off(NA, row, k0)) = val;
+  }
+}
+
+// ---------------------------------------------------------------- the iteration kernel
+
+template <int NA>
+__global__ void __launch_bounds__(kThreadsTc, 1)
+    scatter_tc_kernel(GridParams g, const float* __restrict__ rcorr, const uint8_t* __restrict__ cls,
+                      const float* __restrict__ cls_ds, int ncls, const uint16_t* __restrict__ Pbf,
+                      const float* __restrict__ Q, const float* __restrict__ mut, const float* __restrict__ eps,
+                      const float* __restrict__ nidx, float* __restrict__ Iring, float* __restrict__ Sring,
+                      float tol, int max_iters, RunState rs) {
+  using C = Tc<NA>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sB = smem + C::OFF_B;
+  uint8_t* sAhi = smem + C::OFF_AHI;
+  uint8_t* sAlo = smem + C::OFF_ALO;
+  float* b1t = reinterpret_cast<float*>(smem + C::OFF_B1T);
+  float* sR = reinterpret_cast<float*>(smem + C::OFF_R);
+  uint8_t* sCls = smem + C::OFF_CLS;
+
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int tile_s;
+  __shared__ int plane_s;
+  __shared__ float e_s[kM], rho_s[kM], best_s[kM];
+  __shared__ float red_d[kGroups][kM], red_s[kGroups][kM];
+  __shared__ int act_s[kM], newly_s[kM], stall_s[kM], iters_s[kM];
+  __shared__ double esum_s[kThreadsTc / 32];
+  __shared__ float smax_s[kThreadsTc / 32];
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int row = ((warp & 3) << 5) + lane;
+  const int half = warp >> 2;  // column group
+  const int cb = half * C::HALF;
+  const int n = *rs.step;
+  const size_t plane = static_cast<size_t>(g.nv);
+  const float s_glob = __uint_as_float(rs.smax[(n - 1) & 1]);
+  const bool has_prev = (n - 1) >= g.hist_from;
+  const size_t prev_base = static_cast<size_t>(ring_slot(n - 1)) * g.na * plane;
+  const size_t cur_base = static_cast<size_t>(ring_slot(n)) * g.na * plane;
+  const int ntiles = (g.nv + kM - 1) / kM;
+
+  // ---- one-time set-up: TMEM, barrier, B operand, correction and class tables
+  if (warp == 0) tmem_alloc(&tmem_base_s, C::TCOLS);
+  if (tid == 0) {
+    mbar_init(&mbar);
+    plane_s = g.nv;
+  }
+  load_b_operand<NA>(sB, Pbf);
+  for (int i = tid; i < NA; i += blockDim.x) {
+    sR[i] = rcorr[i];
+    sCls[i] = cls[i];
+  }
+  // zero the K padding of both A operands once (columns >= NA are never written again)
+  if constexpr (C::KP > NA) {
+    for (int u = tid; u < kM * (C::KP - NA) / 8; u += blockDim.x) {
+      const int r = u / ((C::KP - NA) / 8);
+      const int k0 = NA + (u % ((C::KP - NA) / 8)) * 8;
+      *reinterpret_cast<uint4*>(sAhi + sw128_chunk_off(kM, r, k0)) = make_uint4(0u, 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(sAlo + sw128_chunk_off(kM, r, k0)) = make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_s;
+  const uint32_t t_row = tmem + (static_cast<uint32_t>((warp & 3) << 5) << 16);
+  const uint32_t aHi = smem_u32(sAhi), aLo = smem_u32(sAlo), bB = smem_u32(sB);
+  uint32_t phase = 0;
+  bool aborted = false;
+  double esum = 0.0;
+  float smax_loc = 0.0f;
+
+  float q[C::HALF];
+
+  while (true) {
+    if (tid == 0) tile_s = atomicAdd(rs.tile_ctr + (n & 1), 1);
+    __syncthreads();
+    const int tile = tile_s;
+    if (tile >= ntiles) break;
+    const int v0 = tile * kM;
+    const int v = v0 + row;
+    const bool vin = v < g.nv;
+
+    // per-row constants and the b1 table over ds classes
+    if (tid < kM) {
+      const int vv = v0 + tid;
+      float ev = 1.0f, rho = 0.0f;
+      if (vv < g.nv) {
+        ev = eps[vv];
+        const float xm = mut[vv] * g.ds_max;
+        rho = (1.0f - ev) * ray_b1(xm, expf(-xm));
+      }
+      e_s[tid] = ev;
+      rho_s[tid] = rho;
+      best_s[tid] = 3.0e38f;
+      stall_s[tid] = 0;
+      iters_s[tid] = 0;
+      act_s[tid] = vv < g.nv ? 1 : 0;
+      newly_s[tid] = 0;
+    }
+    for (int u = tid; u < ncls * kM; u += blockDim.x) {
+      const int k = u / kM, r = u % kM;
+      const int vv = v0 + r;
+      const float x = vv < g.nv ? mut[vv] * cls_ds[k] : 0.0f;
+      b1t[k * kM + r] = vv < g.nv ? ray_b1(x, expf(-x)) : 0.0f;
+    }
+    __syncthreads();
+
+    // Warm start S(n-1): S_old -> TMEM, X_0 = Q + b1 S_old -> (X_hi, X_lo).  One chunk of
+    // columns at a time (not unrolled) so that the chunk loads are not batched; Q is
+    // re-read here and kept in registers only for the iteration loop below.
+#pragma unroll 1
+    for (int ch = 0; ch < C::NCH; ++ch) {
+      const int c0 = cb + ch * C::CH;
+      float so[C::CH];
+      uint32_t hi[C::CH / 2], lo[C::CH / 2];
+#pragma unroll
+      for (int j = 0; j < C::CH; ++j)
+        so[j] = (vin && has_prev) ? Sring[prev_base + static_cast<size_t>(c0 + j) * plane + v] : 0.0f;
+#pragma unroll
+      for (int j = 0; j < C::CH; j += 2) {
+        const float q0 = vin ? __ldg(Q + static_cast<size_t>(c0 + j) * plane + v) : 0.0f;
+        const float q1 = vin ? __ldg(Q + static_cast<size_t>(c0 + j + 1) * plane + v) : 0.0f;
+        const float x0 = q0 + b1t[sCls[c0 + j] * kM + row] * so[j];
+        const float x1 = q1 + b1t[sCls[c0 + j + 1] * kM + row] * so[j + 1];
+        split_bf16x2(x0, x1, hi[j / 2], lo[j / 2]);
+      }
+      tmem_st<C::CH>(t_row + C::SOFF + c0, so);
+#pragma unroll
+      for (int j = 0; j < C::CH; j += 8) {
+        *reinterpret_cast<uint4*>(sAhi + sw128_chunk_off(kM, row, c0 + j)) =
+            make_uint4(hi[j / 2], hi[j / 2 + 1], hi[j / 2 + 2], hi[j / 2 + 3]);
+        *reinterpret_cast<uint4*>(sAlo + sw128_chunk_off(kM, row, c0 + j)) =
+            make_uint4(lo[j / 2], lo[j / 2 + 1], lo[j / 2 + 2], lo[j / 2 + 3]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < C::HALF; ++c)
+      q[c] = vin ? __ldg(Q + static_cast<size_t>(cb + c) * plane + v) : 0.0f;
+    tmem_wait_st();
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      issue_mmas<NA>(tmem, aHi, aLo, bB);
+      mma_commit(&mbar);
+    }
+
+    int k = 0;
+    int n_active = 1;
+    while (true) {
+      ++k;
+      const bool ok = mbar_wait_bounded(&mbar, phase);
+      phase ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        aborted = true;
+        break;
+      }
+      tc_fence_after();
+      const float ev = e_s[row];
+      const bool act = act_s[row] != 0;
+      // Read the per-column tables through volatile views: they are loop-invariant, and if
+      // the compiler hoists them out of the iteration loop they cost ~190 registers.
+      const volatile float* vb1t = b1t;
+      const volatile float* vR = sR;
+      const volatile uint8_t* vCls = sCls;
+      float dmax = 0.0f, smax = 0.0f;
+      // tcgen05.ld / st are warp-collective: a warp with any active row runs them on every
+      // lane; inactive lanes keep S_old (so they rewrite the same X) and report no change.
+      if (__any_sync(0xffffffffu, act)) {
+#pragma unroll
+        for (int ch = 0; ch < C::NCH; ++ch) {
+          const int c0 = cb + ch * C::CH;
+          float y[C::CH], so[C::CH];
+          tmem_ld<C::CH>(t_row + c0, y);
+          tmem_ld<C::CH>(t_row + C::SOFF + c0, so);
+          tmem_wait_ld();
+          uint32_t hi[C::CH / 2], lo[C::CH / 2];
+#pragma unroll
+          for (int j = 0; j < C::CH; j += 2) {
+            float xn[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              const float b1 = vb1t[vCls[c0 + j + e] * kM + row];
+              const float qv = q[ch * C::CH + j + e];
+              const float xo = fmaf(b1, so[j + e], qv);              // X used by this iteration's MMA
+              const float yc = fmaf(vR[c0 + j + e], xo, y[j + e]);   // D + r X
+              const float sn = act ? fmaf(-ev, yc, yc) : so[j + e];  // S_new = (1 - eps) Y
+              dmax = fmaxf(dmax, fabsf(sn - so[j + e]));
+              smax = fmaxf(smax, fabsf(sn));
+              so[j + e] = sn;
+              xn[e] = fmaf(b1, sn, qv);                              // X for the next MMA
+            }
+            split_bf16x2(xn[0], xn[1], hi[j / 2], lo[j / 2]);
+          }
+          tmem_st<C::CH>(t_row + C::SOFF + c0, so);
+#pragma unroll
+          for (int j = 0; j < C::CH; j += 8) {
+            *reinterpret_cast<uint4*>(sAhi + sw128_chunk_off(kM, row, c0 + j)) =
+                make_uint4(hi[j / 2], hi[j / 2 + 1], hi[j / 2 + 2], hi[j / 2 + 3]);
+            *reinterpret_cast<uint4*>(sAlo + sw128_chunk_off(kM, row, c0 + j)) =
+                make_uint4(lo[j / 2], lo[j / 2 + 1], lo[j / 2 + 2], lo[j / 2 + 3]);
+          }
+        }
+        tmem_wait_st();
+      }
+      red_d[half][row] = dmax;
+      red_s[half][row] = smax;
+      fence_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      // per-voxel stop decision (one thread per row)
+      int still = 0;
+      if (tid < kM) {
+        newly_s[tid] = 0;
+        if (act_s[tid]) {
+          float D = red_d[0][tid], Sm = red_s[0][tid];
+#pragma unroll
+          for (int gi = 1; gi < kGroups; ++gi) {
+            D = fmaxf(D, red_d[gi][tid]);
+            Sm = fmaxf(Sm, red_s[gi][tid]);
+          }
+          const float r = rho_s[tid];
+          if (D < best_s[tid]) {
+            best_s[tid] = D;
+            stall_s[tid] = 0;
+          } else {
+            stall_s[tid] += 1;
+          }
+          const float scale = fmaxf(Sm, 1e-6f * s_glob);
+          // error bound within tol, or the change stopped shrinking (noise floor)
+          const bool conv = (r / (1.0f - r)) * D <= tol * scale || stall_s[tid] >= 3;
+          if (conv || k >= max_iters) {
+            act_s[tid] = 0;
+            newly_s[tid] = 1;
+            iters_s[tid] = k;
+            if (!conv) atomicAdd(rs.nonconv, 1);
+          } else {
+            still = 1;
+          }
+        }
+      }
+      n_active = __syncthreads_count(still);
+      if (n_active > 0 && tid == 0) {
+        tc_fence_after();
+        issue_mmas<NA>(tmem, aHi, aLo, bB);
+        mma_commit(&mbar);
+      }
+      // write out the voxels that stopped in this iteration: I = Q + b1 S, S.  The
+      // addresses derive from a volatile shared copy of the plane size so the compiler
+      // cannot hoist 2 x HALF 64-bit addresses out of the iteration loop into registers.
+      const bool mine = newly_s[row] != 0;
+      if (__any_sync(0xffffffffu, mine)) {  // warp-uniform: the TMEM loads are collective
+        const size_t pl = static_cast<size_t>(*reinterpret_cast<volatile const int*>(&plane_s));
+        float* pI = Iring + cur_base + static_cast<size_t>(cb) * pl + v;
+        float* pS = Sring + cur_base + static_cast<size_t>(cb) * pl + v;
+        const float* pQ = Q + static_cast<size_t>(cb) * pl + v;
+        float esum_row = 0.0f;
+#pragma unroll
+        for (int ch = 0; ch < C::NCH; ++ch) {
+          const int c0 = cb + ch * C::CH;
+          float so[C::CH];
+          tmem_ld<C::CH>(t_row + C::SOFF + c0, so);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < C::CH; ++j) {
+            if (mine) {
+              const float Iv = fmaf(vb1t[vCls[c0 + j] * kM + row], so[j], __ldg(pQ));
+              *pI = Iv;
+              *pS = so[j];
+              esum_row += Iv;
+              smax_loc = fmaxf(smax_loc, fabsf(so[j]));
+            }
+            pI += pl;
+            pS += pl;
+            pQ += pl;
+          }
+        }
+        if (mine) esum += static_cast<double>(esum_row) * static_cast<double>(nidx[v]);
+      }
+      if (n_active == 0) break;
+    }
+    if (aborted) break;
+    // iteration statistics of this tile
+    if (warp < 4) {
+      int it = (v0 + tid < g.nv) ? iters_s[tid] : 0;
+      unsigned long long is = static_cast<unsigned long long>(it);
+      int im = it;
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) {
+        im = max(im, __shfl_xor_sync(0xffffffffu, im, o));
+        is += __shfl_xor_sync(0xffffffffu, is, o);
+      }
+      if (lane == 0) {
+        atomicMax(rs.iters_max + n, im);
+        atomicAdd(rs.iters_sum + n, is);
+      }
+    }
+    __syncthreads();
+  }
+
+  if (aborted && tid == 0) atomicExch(rs.error, 2);
+  // energy and max |S| of this CTA's voxels
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    esum += __shfl_xor_sync(0xffffffffu, esum, o);
+    smax_loc = fmaxf(smax_loc, __shfl_xor_sync(0xffffffffu, smax_loc, o));
+  }
+  if (lane == 0) {
+    esum_s[warp] = esum;
+    smax_s[warp] = smax_loc;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0) {
+    double e = 0.0;
+    float sm = 0.0f;
+    for (int w = 0; w < kThreadsTc / 32; ++w) {
+      e += esum_s[w];
+      sm = fmaxf(sm, smax_s[w]);
+    }
+    atomicAdd(rs.energy + n, e * static_cast<double>(g.e_scale));
+    atomicMax(rs.smax + (n & 1), __float_as_uint(sm));
+  }
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, C::TCOLS);
+  }
+}
+
+// ---------------------------------------------------------------- tile self-test kernel
+// One CTA: D = A B^T for one 128 x NA tile with A [128][KP], B [NA][KP] (bf16, K padded
+// with zeros), using the same operand layouts, descriptors and TMEM read-out as the
+// iteration kernel; D [128][NA] fp32.
+template <int NA>
+__global__ void __launch_bounds__(kThreadsTc, 1)
+    tc_tile_selftest_kernel(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, float* __restrict__ D,
+                            int* __restrict__ err) {
+  using C = Tc<NA>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sB = smem + C::OFF_B;
+  uint8_t* sA = smem + C::OFF_AHI;
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tmem_base_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) tmem_alloc(&tmem_base_s, C::TCOLS);
+  if (tid == 0) mbar_init(&mbar);
+  for (int u = tid; u < NA * C::KB * 8; u += blockDim.x) {
+    const int r = u / (C::KB * 8), rem = u % (C::KB * 8);
+    const int k0 = (rem / 8) * 64 + (rem % 8) * 8;
+    *reinterpret_cast<uint4*>(sB + sw128_chunk_off(NA, r, k0)) =
+        *reinterpret_cast<const uint4*>(B + static_cast<size_t>(r) * C::KP + k0);
+  }
+  for (int u = tid; u < kM * C::KB * 8; u += blockDim.x) {
+    const int r = u / (C::KB * 8), rem = u % (C::KB * 8);
+    const int k0 = (rem / 8) * 64 + (rem % 8) * 8;
+    *reinterpret_cast<uint4*>(sA + sw128_chunk_off(kM, r, k0)) =
+        *reinterpret_cast<const uint4*>(A + static_cast<size_t>(r) * C::KP + k0);
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  const uint32_t tmem = tmem_base_s;
+  if (tid == 0) {
+    tc_fence_after();
+    const uint32_t a = smem_u32(sA), b = smem_u32(sB);
+#pragma unroll
+    for (int s = 0; s < C::KSTEPS; ++s) {
+      const uint32_t ko = static_cast<uint32_t>((s & 3) * 32), kb = static_cast<uint32_t>(s >> 2);
+      mma_bf16(tmem, sw128_desc(a + kb * kM * 128 + ko), sw128_desc(b + kb * NA * 128 + ko), C::IDESC,
+               s > 0 ? 1u : 0u);
+    }
+    mma_commit(&mbar);
+  }
+  const bool ok = mbar_wait_bounded(&mbar, 0);
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) *err = 2;
+  } else {
+    tc_fence_after();
+    const int row = ((warp & 3) << 5) + lane;
+    const int cb = (warp >> 2) * C::HALF;
+    const uint32_t t_row = tmem + (static_cast<uint32_t>((warp & 3) << 5) << 16);
+#pragma unroll
+    for (int ch = 0; ch < C::NCH; ++ch) {
+      float y[C::CH];
+      tmem_ld<C::CH>(t_row + cb + ch * C::CH, y);
+      tmem_wait_ld();
+#pragma unroll
+      for (int j = 0; j < C::CH; ++j) D[static_cast<size_t>(row) * NA + cb + ch * C::CH + j] = y[j];
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, C::TCOLS);
+  }
+}
+
+int g_num_sms = 0;
+
+template <int NA>
+cudaError_t configure() {
+  cudaError_t e = cudaFuncSetAttribute(scatter_tc_kernel<NA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       Tc<NA>::SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(tc_tile_selftest_kernel<NA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              Tc<NA>::SMEM);
+}
+
+}  // namespace
+
+bool scatter_bf16_supported(int na) {
+  if (na != 48 && na != 192) return false;
+  if (g_num_sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
+    if (configure<48>() != cudaSuccess || configure<192>() != cudaSuccess) {
+      g_num_sms = 0;
+      return false;
+    }
+  }
+  return true;
+}
+
+cudaError_t launch_scatter_bf16(const GridParams& g, const BfTables& t, const uint16_t* Pbf, const float* Q,
+                                const float* mut, const float* eps, const float* nidx, float* Iring,
+                                float* Sring, float tol, int max_iters, RunState rs, cudaStream_t st) {
+  const int ntiles = (g.nv + kM - 1) / kM;
+  const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
+  if (g.na == 48) {
+    scatter_tc_kernel<48><<<grid, kThreadsTc, Tc<48>::SMEM, st>>>(g, t.rcorr, t.cls, t.cls_ds, t.ncls, Pbf, Q, mut,
+                                                                  eps, nidx, Iring, Sring, tol, max_iters, rs);
+  } else if (g.na == 192) {
+    scatter_tc_kernel<192><<<grid, kThreadsTc, Tc<192>::SMEM, st>>>(g, t.rcorr, t.cls, t.cls_ds, t.ncls, Pbf, Q,
+                                                                    mut, eps, nidx, Iring, Sring, tol, max_iters, rs);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t tc_tile_selftest(int na, const uint16_t* A, const uint16_t* B, float* D, int* err, cudaStream_t st) {
+  if (!scatter_bf16_supported(na)) return cudaErrorNotSupported;
+  if (na == 48)
+    tc_tile_selftest_kernel<48><<<1, kThreadsTc, Tc<48>::SMEM, st>>>(A, B, D, err);
+  else
+    tc_tile_selftest_kernel<192><<<1, kThreadsTc, Tc<192>::SMEM, st>>>(A, B, D, err);
+  return cudaGetLastError();
 }
 
 }  // namespace trinity

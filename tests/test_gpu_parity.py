@@ -1,11 +1,15 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle.
 
-Tolerances (FP32 mode).  The GPU stops its source iteration when its error bound
-reaches tol = 1e-6 relative (or FP32 resolution), the oracle is run to 1e-10, and FP32
-rounding of the ~200-term angular sums adds ~1e-7 relative per iteration, damped by the
-contraction; fields and detector curves are therefore required to agree to 1e-5
-relative to their peak (detector bins below 1e-6 of the peak are not compared
-relatively).
+Tolerances (FP32 mode).  The oracle runs its source iteration to 1e-10 (the fixed point
+to FP64 accuracy).  The GPU runs with tol = 1e-7, so it stops at the noise floor of FP32
+arithmetic (its stall exit), where the iterate fluctuates around the fixed point by the
+rounding of the ~200-term angular sums (~1e-7 relative, amplified at most rho/(1-rho)
+~ 11 times at the workloads' optics).  A float32 emulation of the oracle puts that
+floor near 2e-6 of the field peak after 20-100 steps; fields, energy and detector curves
+are required to agree to 1e-5 relative to their peak, and detector bins above 1e-6 of
+the peak to 5e-4 each.  At the workloads' own tol = 1e-6 both sides stop up to 1e-6 from
+the fixed point (one-sided: the iteration approaches monotonically) and the bias adds
+up over steps, so that case is compared against the oracle at the same tol.
 """
 import numpy as np
 import pytest
@@ -44,13 +48,16 @@ def _check_detectors(got, ref, tol):
     assert _rel_peak(got, ref) <= tol
     big = np.abs(ref) > 1e-6 * peak
     rel = np.abs(got[big] - ref[big]) / np.abs(ref[big])
-    assert rel.max() <= 50 * tol, rel.max()
+    assert rel.max() <= 5e-4, rel.max()
+
+
+GPU_TOL = 1e-7
 
 
 @pytest.fixture(scope="module")
 def small_run():
     T = _gpu()
-    prob = W.config_small(steps=100)
+    prob = W.config_small(steps=100, tol=GPU_TOL)
     fwd = T.Forward(prob)
     iters = fwd.step(100)
     out = dict(det=fwd.detectors(), energy=fwd.energy(), I=fwd.field(T.FIELD_I),
@@ -82,9 +89,21 @@ def test_small_config_fields_elementwise(small_run):
 
 def test_small_config_iteration_counts_plausible(small_run):
     out, ref = small_run
-    # same stop rule, looser tolerance on the GPU (1e-6 vs the oracle's 1e-10)
+    # the GPU (tol 1e-7, stall exit) needs no more iterations than the oracle at 1e-10
     assert np.all(out["iters"] >= 1)
     assert np.all(out["iters"][2:] <= np.array(ref.iters_max)[2:] + 5)
+
+
+def test_small_config_at_workload_tolerance():
+    """At the workload's tol = 1e-6, against the oracle at the same tolerance."""
+    T = _gpu()
+    prob = W.config_small(steps=100, tol=1e-6)
+    fwd = T.Forward(prob)
+    fwd.step(100)
+    ref = _oracle(prob, 100, tol=1e-6)
+    _check_detectors(fwd.detectors(), ref.det, FP32_TOL)
+    assert _rel_peak(fwd.field(T.FIELD_I), ref.level("I")) <= FP32_TOL
+    fwd.close()
 
 
 @pytest.mark.parametrize("shape,nside,steps", [((13, 11, 9), 2, 30), ((9, 7, 12), 4, 24),
@@ -94,7 +113,7 @@ def test_ragged_grids(shape, nside, steps):
     resolution, a source on a side face and detectors on several faces."""
     T = _gpu()
     nx, ny, nz = shape
-    prob = W.homogeneous(nx, ny, nz, nside, 0.02, 3.0, steps=steps)
+    prob = W.homogeneous(nx, ny, nz, nside, 0.02, 3.0, steps=steps, tol=GPU_TOL)
     prob["source"] = dict(face=2, u_mm=nx / 2, v_mm=nz / 2, half_angle_deg=15.0, pulse_steps=2,
                           energy=1.0)
     prob["detectors"] = [dict(face=2, u_mm=nx / 2 + 2.5, v_mm=nz / 2, radius_mm=1.2, half_angle_deg=15.0),
@@ -113,7 +132,8 @@ def test_heterogeneous_optics_small():
     """Air cylinder (n = 1, no scattering) and absorbing spheres at a quarter of the
     heterogeneous workload's size: per-voxel delays, albedo zero, strong absorbers."""
     T = _gpu()
-    prob = W.config_hetero(steps=30, precision="fp32", nx=32, ny=32, nz=24, nside=2, scale=0.25)
+    prob = W.config_hetero(steps=30, precision="fp32", nx=32, ny=32, nz=24, nside=2, scale=0.25,
+                           tol=GPU_TOL)
     fwd = T.Forward(prob)
     fwd.step(30)
     ref = _oracle(prob, 30)
