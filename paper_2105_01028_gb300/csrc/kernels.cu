@@ -210,19 +210,32 @@ __global__ void __launch_bounds__(ScatterCfg<NA>::kThreads)
 #pragma unroll
     for (int v = 0; v < kTile; ++v) acc[v] = 0.0f;
     if (live) {
+      // Blocked accumulation: each block of kBlk terms is summed on its own and then added
+      // to the total, which keeps the rounding noise of the ~200-term sum close to that of
+      // a pairwise sum.  The iteration's attainable accuracy is set by that noise, divided
+      // by (1 - rho) ~ 0.07 at the workloads' optics.
+      constexpr int kBlk = (NA % 8 == 0) ? 8 : 4;
       const float* pcol = P + i;
-#pragma unroll 4
-      for (int j = 0; j < NA; ++j) {
-        const float p = __ldg(pcol + static_cast<size_t>(j) * NA);
-        const float4* xr = reinterpret_cast<const float4*>(&Xs[cur][j][0]);
+#pragma unroll 1
+      for (int j0 = 0; j0 < NA; j0 += kBlk) {
+        float t[kTile];
 #pragma unroll
-        for (int v4 = 0; v4 < kTile / 4; ++v4) {
-          const float4 x4 = xr[v4];
-          acc[4 * v4 + 0] = fmaf(p, x4.x, acc[4 * v4 + 0]);
-          acc[4 * v4 + 1] = fmaf(p, x4.y, acc[4 * v4 + 1]);
-          acc[4 * v4 + 2] = fmaf(p, x4.z, acc[4 * v4 + 2]);
-          acc[4 * v4 + 3] = fmaf(p, x4.w, acc[4 * v4 + 3]);
+        for (int v = 0; v < kTile; ++v) t[v] = 0.0f;
+#pragma unroll
+        for (int j = j0; j < j0 + kBlk; ++j) {
+          const float p = __ldg(pcol + static_cast<size_t>(j) * NA);
+          const float4* xr = reinterpret_cast<const float4*>(&Xs[cur][j][0]);
+#pragma unroll
+          for (int v4 = 0; v4 < kTile / 4; ++v4) {
+            const float4 x4 = xr[v4];
+            t[4 * v4 + 0] = fmaf(p, x4.x, t[4 * v4 + 0]);
+            t[4 * v4 + 1] = fmaf(p, x4.y, t[4 * v4 + 1]);
+            t[4 * v4 + 2] = fmaf(p, x4.z, t[4 * v4 + 2]);
+            t[4 * v4 + 3] = fmaf(p, x4.w, t[4 * v4 + 3]);
+          }
         }
+#pragma unroll
+        for (int v = 0; v < kTile; ++v) acc[v] += t[v];
       }
     }
     // epilogue: S_new = a * acc on active voxels; X = Q + b1 * S for the next iteration

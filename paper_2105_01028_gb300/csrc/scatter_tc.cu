@@ -195,6 +195,29 @@ __device__ __forceinline__ uint32_t sw128_chunk_off(int rows, int r, int k0) {
   return static_cast<uint32_t>(kb * rows * 128 + r * 128 + ((ch ^ (r & 7)) << 4));
 }
 
+// Shared-memory vector loads issued as volatile asm: the tables they read are constant
+// over the iteration loop, and without this the compiler hoists every chunk's values
+// out of the loop into registers (far more than the register budget).
+template <int N>
+__device__ __forceinline__ void lds_vec(const float* p, float (&v)[N]) {
+  const uint32_t a = smem_u32(p);
+#pragma unroll
+  for (int i = 0; i < N; i += 4)
+    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v[i]), "=f"(v[i + 1]), "=f"(v[i + 2]), "=f"(v[i + 3])
+                 : "r"(a + 4 * i));
+}
+
+template <int N>
+__device__ __forceinline__ void lds_bytes(const uint8_t* p, uint32_t (&v)[N / 4]) {
+  const uint32_t a = smem_u32(p);
+  if constexpr (N == 16) {
+    asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]) : "r"(a));
+  } else {
+    asm volatile("ld.shared.v2.u32 {%0,%1}, [%2];" : "=r"(v[0]), "=r"(v[1]) : "r"(a));
+  }
+}
+
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   const __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const uint32_t*>(&b);
@@ -408,7 +431,6 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       // Read the per-column tables through volatile views: they are loop-invariant, and if
       // the compiler hoists them out of the iteration loop they cost ~190 registers.
       const volatile float* vb1t = b1t;
-      const volatile float* vR = sR;
       const volatile uint8_t* vCls = sCls;
       float dmax = 0.0f, smax = 0.0f;
       // tcgen05.ld / st are warp-collective: a warp with any active row runs them on every
@@ -422,15 +444,20 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
           tmem_ld<C::CH>(t_row + C::SOFF + c0, so);
           tmem_wait_ld();
           uint32_t hi[C::CH / 2], lo[C::CH / 2];
+          float rv[C::CH];
+          uint32_t cv[C::CH / 4];
+          lds_vec<C::CH>(sR + c0, rv);
+          lds_bytes<C::CH>(sCls + c0, cv);
 #pragma unroll
           for (int j = 0; j < C::CH; j += 2) {
             float xn[2];
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
-              const float b1 = vb1t[vCls[c0 + j + e] * kM + row];
+              const int cl = static_cast<int>((cv[(j + e) >> 2] >> (8 * ((j + e) & 3))) & 0xffu);
+              const float b1 = vb1t[cl * kM + row];
               const float qv = q[ch * C::CH + j + e];
               const float xo = fmaf(b1, so[j + e], qv);              // X used by this iteration's MMA
-              const float yc = fmaf(vR[c0 + j + e], xo, y[j + e]);   // D + r X
+              const float yc = fmaf(rv[j + e], xo, y[j + e]);        // D + r X
               const float sn = act ? fmaf(-ev, yc, yc) : so[j + e];  // S_new = (1 - eps) Y
               dmax = fmaxf(dmax, fabsf(sn - so[j + e]));
               smax = fmaxf(smax, fabsf(sn));
@@ -455,6 +482,14 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       fence_async_smem();
       tc_fence_before();
       __syncthreads();
+      // The next MMA only needs the X just written, so it is issued before the stop
+      // decision and overlaps the decision and the write-out.  If every row stops in this
+      // iteration, that MMA is not needed; it is waited for before the tile ends.
+      if (tid == 0) {
+        tc_fence_after();
+        issue_mmas<NA>(tmem, aHi, aLo, bB);
+        mma_commit(&mbar);
+      }
       // per-voxel stop decision (one thread per row)
       int still = 0;
       if (tid < kM) {
@@ -487,11 +522,6 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         }
       }
       n_active = __syncthreads_count(still);
-      if (n_active > 0 && tid == 0) {
-        tc_fence_after();
-        issue_mmas<NA>(tmem, aHi, aLo, bB);
-        mma_commit(&mbar);
-      }
       // write out the voxels that stopped in this iteration: I = Q + b1 S, S.  The
       // addresses derive from a volatile shared copy of the plane size so the compiler
       // cannot hoist 2 x HALF 64-bit addresses out of the iteration loop into registers.
@@ -524,7 +554,15 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         }
         if (mine) esum += static_cast<double>(esum_row) * static_cast<double>(nidx[v]);
       }
-      if (n_active == 0) break;
+      if (n_active == 0) {
+        // drain the MMA issued above, so the barrier's phase and the tensor memory are
+        // free for the next tile
+        const bool ok2 = mbar_wait_bounded(&mbar, phase);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok2)) aborted = true;
+        tc_fence_after();
+        break;
+      }
     }
     if (aborted) break;
     // iteration statistics of this tile
