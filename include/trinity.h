@@ -100,6 +100,19 @@ int trinity_set_optics(trinity_ctx* ctx, const float* mua, const float* mus, con
                        double g, int ptr_kind);
 int trinity_set_optics_uniform(trinity_ctx* ctx, double mua, double mus, double g, double n);
 
+/* Refraction and reflection at refractive-index steps (Eqs. 13-14; Section 3.3 applies
+ * them at the grid points next to a region of different index).  With ``on`` set, at
+ * every voxel whose upwind ray sample lies in a voxel of different n, the light arriving
+ * along that direction is split, after the sweep and before the source iteration, into
+ * the specular direction (Fresnel reflectance R, Eq. 14) and the Snell direction (1 - R,
+ * Eq. 13), each snapped to the nearest pixel; the interface normal is the
+ * central-difference gradient of the n map.  The split conserves photons.  The table is
+ * rebuilt from the n map of each trinity_set_optics call.  Before the first step. */
+int trinity_set_fresnel(trinity_ctx* ctx, int on);
+
+/* Number of interface voxels in the context's current table. */
+int trinity_interface_count(const trinity_ctx* ctx, int* n);
+
 /* Collimated pulse (Section 3.1): enters through the face voxel containing (u_mm, v_mm)
  * of ``face``, within a cone of ``half_angle_deg`` around the inward normal, during the
  * first ``pulse_steps`` time levels, carrying ``energy`` in total.  The cone's solid
@@ -189,6 +202,14 @@ int trinity_phase_matrix(int nside, double g, double* out, size_t n, double* g_e
  * (int8 [N_a][2][max(nx,ny,nz)]). */
 int trinity_lattice_tables(int nside, int nx, int ny, int nz, double h_mm, int periodic,
                            int32_t* dom_sgn, double* ds, int8_t* offsets, size_t n_offsets);
+
+/* The interface split of trinity_set_fresnel for an n map ([nz][ny][nx] float32), as
+ * entries (voxel, arriving direction j, receiving direction d, weight), sorted by voxel
+ * then j; *count receives the number of entries.  Pass NULL outputs (or cap too small)
+ * to query the count only. */
+int trinity_interface_entries(int nside, int nx, int ny, int nz, double h_mm, int periodic,
+                              const float* nmap, int* vox, int* j, int* d, double* w, size_t cap,
+                              size_t* count);
 
 /* Cone weights alpha_d (double [N_a]) of a face: the fraction of a cap of half_angle_deg
  * around the inward (inward = 1) or outward normal nearest to each direction. */

@@ -28,6 +28,9 @@ Per voxel v and direction d, at time level n (time step dt):
   stopped iterate is within tol of the fixed point relative to the voxel's own source,
   and S_glob = max |S(n-1)| over the whole grid.  The floor matters where the fixed point
   is zero (the pulse has passed, Q = 0): there a purely relative test never holds.
+* Index interfaces (§3.3, Eqs. 13-14; reading in ``fresnel``): with ``fresnel`` set, Q of
+  the directions whose segment crosses an index step is split into the specular and
+  Snell directions before the source iteration.
 * Boundaries: absorbing ("vacuum", §3.1: photons reaching the box boundary are lost,
   nothing re-enters) or periodic (test configuration).  The pulse enters through the
   face voxel of the source spot, for the directions of the source cone, during the
@@ -43,6 +46,7 @@ from .healpix import ring_directions, pixel_weight
 from .phase import phase_matrix
 from .geometry import RayLattice, face_axes, floor_snapped
 from .cones import cone_fractions, cap_solid_angle
+from .fresnel import interface_operators, apply_interfaces
 
 SERIES_X = 1e-3  # below this optical depth the Eq. 9 weights use their Taylor series
 FLOOR = 1e-6     # absolute stop floor, relative to the grid-wide max |S| of the previous level
@@ -189,6 +193,9 @@ class Model:
         self.bin_width = float(prob.get("bin_ps", 10.0)) * 1e-3
         self.nbins = int(prob.get("nbins", 1))
 
+        # index interfaces (Eqs. 13-14)
+        self.interfaces = interface_operators(self) if prob.get("fresnel", False) else {}
+
         # face outflow for the escaped-energy tally
         self.faces = []
         if not self.periodic:
@@ -301,6 +308,8 @@ class Solver:
         I_up = _retarded(self._hist, seg, n, "I", m)
         S_up = _retarded(self._hist, seg, n, "S", m)
         Q = I_up * seg["T"] + S_up * seg["b0"]
+        if m.interfaces:
+            apply_interfaces(m.interfaces, Q)
         if n > 0 or self.hist_from < 0:
             S_prev = self.S[(n - 1) % RING_DEPTH]
         else:
@@ -361,6 +370,10 @@ def one_step_at(model, n, hist, voxels, s_glob):
     S_up = _retarded(hist, seg, n, "S", model)
     Q = I_up * seg["T"] + S_up * seg["b0"]
     vox = seg["vox"]
+    if model.interfaces:
+        pos = {int(v): k for k, v in enumerate(vox)}
+        sub = {pos[v]: ops for v, ops in model.interfaces.items() if v in pos}
+        apply_interfaces(sub, Q)
     lev = np.full(vox.shape, n - 1)
     S_prev = np.stack([hist("S", lev, np.full(vox.shape, d), vox) for d in range(model.na)])
     S, iters = source_iteration(model, Q, seg["b1"], S_prev, model.albedo[vox], s_glob)

@@ -68,6 +68,8 @@ class Forward:
         self.nv = desc.nx * desc.ny * desc.nz
         self.na = 12 * desc.nside * desc.nside
         self._check(self.set_optics(prob["mua"], prob["mus"], prob["nidx"], prob["g"]))
+        if prob.get("fresnel", False):
+            self._check(self.L.trinity_set_fresnel(self.h, 1))
         src = prob.get("source")
         if src is not None:
             self._check(self.L.trinity_set_source(self.h, int(src["face"]), float(src["u_mm"]),
@@ -108,6 +110,11 @@ class Forward:
         if not (ka == ks == kn):
             raise ValueError("optics maps must all be host arrays or all device tensors")
         return self.L.trinity_set_optics(self.h, pa, ps, pn, float(g), ka)
+
+    def interface_count(self):
+        n = ctypes.c_int()
+        self._check(self.L.trinity_interface_count(self.h, ctypes.byref(n)))
+        return n.value
 
     def set_initial_state(self, I0, S0):
         pi, ki, keep_i = _ptr(I0)
@@ -215,6 +222,27 @@ def lattice_tables(nside, nx, ny, nz, h=1.0, periodic=False):
     if rc != OK:
         raise TrinityError(rc, "lattice_tables")
     return dom_sgn, ds, offs
+
+
+def interface_entries(nside, nidx, h=1.0, periodic=False):
+    """(voxel, j, d, weight) arrays of the interface split for an n map [nz, ny, nx]."""
+    nm = np.ascontiguousarray(nidx, dtype=np.float32)
+    nz, ny, nx = nm.shape
+    cnt = ctypes.c_size_t()
+    L = lib()
+    args = (nside, nx, ny, nz, float(h), int(periodic), nm.ctypes.data_as(ctypes.c_void_p))
+    rc = L.trinity_interface_entries(*args, None, None, None, None, 0, ctypes.byref(cnt))
+    if rc != OK:
+        raise TrinityError(rc, "interface_entries")
+    n = cnt.value
+    vox, j, d = (np.zeros(n, dtype=np.int32) for _ in range(3))
+    w = np.zeros(n)
+    rc = L.trinity_interface_entries(*args, vox.ctypes.data_as(ctypes.c_void_p), j.ctypes.data_as(ctypes.c_void_p),
+                                     d.ctypes.data_as(ctypes.c_void_p), w.ctypes.data_as(ctypes.c_void_p), n,
+                                     ctypes.byref(cnt))
+    if rc != OK:
+        raise TrinityError(rc, "interface_entries")
+    return vox, j, d, w
 
 
 def cone_weights(nside, face, half_angle_deg, inward):

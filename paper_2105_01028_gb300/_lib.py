@@ -32,6 +32,11 @@ SIGNATURES = {
     "trinity_create_grid": (c_int, [ctypes.POINTER(GridDesc), c_void_p, ctypes.POINTER(c_void_p)]),
     "trinity_set_optics": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_int]),
     "trinity_set_optics_uniform": (c_int, [c_void_p, c_double, c_double, c_double, c_double]),
+    "trinity_set_fresnel": (c_int, [c_void_p, c_int]),
+    "trinity_interface_count": (c_int, [c_void_p, P_int]),
+    "trinity_interface_entries": (c_int, [c_int, c_int, c_int, c_int, c_double, c_int, c_void_p,
+                                          c_void_p, c_void_p, c_void_p, c_void_p, c_size_t,
+                                          ctypes.POINTER(c_size_t)]),
     "trinity_set_source": (c_int, [c_void_p, c_int, c_double, c_double, c_double, c_int, c_double]),
     "trinity_add_detector": (c_int, [c_void_p, c_int, c_double, c_double, c_double, c_double, P_int]),
     "trinity_set_bins": (c_int, [c_void_p, c_double, c_int]),

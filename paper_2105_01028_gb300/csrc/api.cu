@@ -75,6 +75,14 @@ struct trinity_ctx {
 
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
+
+  // index interfaces (Eqs. 13-14)
+  bool fresnel = false;
+  std::vector<float> nmap;  // host copy of the refractive-index map
+  int n_iface = 0;
+  int *d_if_vox = nullptr, *d_if_rowptr = nullptr, *d_if_src = nullptr;
+  float* d_if_w = nullptr;
+  uint8_t* d_if_keep = nullptr;
 };
 
 namespace {
@@ -260,12 +268,54 @@ BfTables bf_tables(trinity_ctx* c) {
   return t;
 }
 
+void free_interfaces(trinity_ctx* c) {
+  cudaFree(c->d_if_vox);
+  cudaFree(c->d_if_rowptr);
+  cudaFree(c->d_if_src);
+  cudaFree(c->d_if_w);
+  cudaFree(c->d_if_keep);
+  c->d_if_vox = c->d_if_rowptr = c->d_if_src = nullptr;
+  c->d_if_w = nullptr;
+  c->d_if_keep = nullptr;
+  c->n_iface = 0;
+}
+
+// Build and upload the interface table from the current n map (host FP64 decisions).
+int build_interface_table(trinity_ctx* ctx) {
+  free_interfaces(ctx);
+  if (!ctx->fresnel || ctx->nmap.empty()) return TRINITY_OK;
+  InterfaceTable T;
+  try {
+    T = build_interfaces(ctx->dirs, ctx->lat, ctx->g.nx, ctx->g.ny, ctx->g.nz, ctx->desc.h_mm,
+                         ctx->g.periodic != 0, ctx->nmap);
+  } catch (const std::exception& e) {
+    return fail(ctx, TRINITY_E_INVALID, e.what());
+  }
+  ctx->n_iface = static_cast<int>(T.vox.size());
+  if (ctx->n_iface == 0) return TRINITY_OK;
+  CK(dalloc(&ctx->d_if_vox, T.vox.size()));
+  CK(dalloc(&ctx->d_if_rowptr, T.rowptr.size()));
+  CK(dalloc(&ctx->d_if_src, T.src.size()));
+  CK(dalloc(&ctx->d_if_w, T.w.size()));
+  CK(dalloc(&ctx->d_if_keep, T.keep.size()));
+  CK(cudaMemcpy(ctx->d_if_vox, T.vox.data(), T.vox.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_if_rowptr, T.rowptr.data(), T.rowptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+  if (!T.src.empty()) {
+    CK(cudaMemcpy(ctx->d_if_src, T.src.data(), T.src.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_if_w, T.w.data(), T.w.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  CK(cudaMemcpy(ctx->d_if_keep, T.keep.data(), T.keep.size(), cudaMemcpyHostToDevice));
+  return TRINITY_OK;
+}
+
 // The launches of one time step (all on ctx->stream; the step index lives on the device).
 int enqueue_step(trinity_ctx* ctx) {
   const RunState rs = run_state(ctx);
   const GridParams& g = ctx->g;
   CK(launch_sweep(g, ctx->d_dirs, ctx->d_offs, ctx->I, ctx->S, ctx->mut, ctx->nidx, ctx->Q, rs,
                   ctx->stream));
+  CK(launch_interface(ctx->n_iface, g.na, ctx->d_if_vox, ctx->d_if_rowptr, ctx->d_if_src, ctx->d_if_w,
+                      ctx->d_if_keep, ctx->Q, g.nv, ctx->stream));
   if (ctx->desc.precision == TRINITY_BF16) {
     CK(launch_scatter_bf16(g, bf_tables(ctx), ctx->Pbf, ctx->Q, ctx->mut, ctx->eps, ctx->nidx, ctx->I,
                            ctx->S, static_cast<float>(ctx->desc.tol), ctx->desc.max_iters, rs,
@@ -494,6 +544,11 @@ int trinity_set_optics(trinity_ctx* ctx, const float* mua, const float* mus, con
   CK(cudaMemcpy(ctx->Pbf, Pb.data(), Pb.size() * 2, cudaMemcpyHostToDevice));
   ctx->g_aniso = g;
   ctx->optics_set = true;
+  ctx->nmap = r;
+  {
+    const int rc2 = build_interface_table(ctx);
+    if (rc2 != TRINITY_OK) return rc2;
+  }
   if (ctx->locked) return trinity_reset(ctx);
   return TRINITY_OK;
 }
@@ -503,6 +558,19 @@ int trinity_set_optics_uniform(trinity_ctx* ctx, double mua, double mus, double 
   const size_t nv = ctx->g.nv;
   std::vector<float> a(nv, float(mua)), s(nv, float(mus)), r(nv, float(n));
   return trinity_set_optics(ctx, a.data(), s.data(), r.data(), g, 0);
+}
+
+int trinity_set_fresnel(trinity_ctx* ctx, int on) {
+  if (!ctx) return TRINITY_E_INVALID;
+  if (ctx->locked) return fail(ctx, TRINITY_E_STATE, "interfaces must be set before the first step");
+  ctx->fresnel = on != 0;
+  return build_interface_table(ctx);
+}
+
+int trinity_interface_count(const trinity_ctx* ctx, int* n) {
+  if (!ctx || !n) return TRINITY_E_INVALID;
+  *n = ctx->n_iface;
+  return TRINITY_OK;
 }
 
 int trinity_set_source(trinity_ctx* ctx, int face, double u_mm, double v_mm, double half_angle_deg,
@@ -719,6 +787,8 @@ int trinity_profile_steps(trinity_ctx* ctx, int nsteps, double* kernel_ms) {
     CK(cudaEventRecord(e[0], ctx->stream));
     CK(launch_sweep(g, ctx->d_dirs, ctx->d_offs, ctx->I, ctx->S, ctx->mut, ctx->nidx, ctx->Q, rs,
                     ctx->stream));
+    CK(launch_interface(ctx->n_iface, g.na, ctx->d_if_vox, ctx->d_if_rowptr, ctx->d_if_src, ctx->d_if_w,
+                        ctx->d_if_keep, ctx->Q, g.nv, ctx->stream));
     CK(cudaEventRecord(e[1], ctx->stream));
     if (ctx->desc.precision == TRINITY_BF16)
       CK(launch_scatter_bf16(g, bf_tables(ctx), ctx->Pbf, ctx->Q, ctx->mut, ctx->eps, ctx->nidx, ctx->I,
@@ -867,6 +937,7 @@ const char* trinity_last_error(const trinity_ctx* ctx) {
 
 void trinity_destroy(trinity_ctx* ctx) {
   if (!ctx) return;
+  free_interfaces(ctx);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   void* bufs[] = {ctx->I,         ctx->S,          ctx->Q,           ctx->mut,       ctx->eps,
                   ctx->nidx,      ctx->P32,        ctx->Pbf,         ctx->d_dirs,    ctx->d_offs,
@@ -949,6 +1020,30 @@ int trinity_lattice_tables(int nside, int nx, int ny, int nz, double h_mm, int p
       if (ds) ds[d] = L.ds[d];
     }
     if (offsets) std::copy(L.off.begin(), L.off.end(), offsets);
+  } catch (...) {
+    return TRINITY_E_INVALID;
+  }
+  return TRINITY_OK;
+}
+
+int trinity_interface_entries(int nside, int nx, int ny, int nz, double h_mm, int periodic,
+                              const float* nmap, int* vox, int* j, int* d, double* w, size_t cap,
+                              size_t* count) {
+  if (nside < 1 || nside > 64 || nx < 1 || ny < 1 || nz < 1 || !(h_mm > 0.0) || !nmap || !count)
+    return TRINITY_E_INVALID;
+  try {
+    const std::vector<double> dirs = healpix_dirs(nside);
+    const Lattice L = build_lattice(dirs, nx, ny, nz, h_mm, periodic != 0);
+    const std::vector<float> nm(nmap, nmap + static_cast<size_t>(nx) * ny * nz);
+    const InterfaceTable T = build_interfaces(dirs, L, nx, ny, nz, h_mm, periodic != 0, nm);
+    *count = T.s_vox.size();
+    if (cap < T.s_vox.size()) return vox ? TRINITY_E_INVALID : TRINITY_OK;
+    for (size_t k = 0; k < T.s_vox.size(); ++k) {
+      if (vox) vox[k] = T.s_vox[k];
+      if (j) j[k] = T.s_j[k];
+      if (d) d[k] = T.s_d[k];
+      if (w) w[k] = T.s_w[k];
+    }
   } catch (...) {
     return TRINITY_E_INVALID;
   }

@@ -130,6 +130,8 @@ cudaError_t launch_tally(const GridParams& g, const DirInfo* dirs, const float* 
                          const int* det_id, int n_det_entries, double* det, int nbins,
                          RunState rs, cudaStream_t st);
 cudaError_t launch_advance(RunState rs, cudaStream_t st);
+cudaError_t launch_interface(int nvox, int na, const int* vox, const int* rowptr, const int* src,
+                             const float* w, const uint8_t* keep, float* Q, int nv, cudaStream_t st);
 bool scatter_bf16_supported(int na);
 cudaError_t launch_scatter_bf16(const GridParams& g, const BfTables& t, const uint16_t* Pbf,
                                 const float* Q, const float* mut, const float* eps,

@@ -243,3 +243,164 @@ std::vector<double> cone_weights(const std::vector<double>& dirs, int face,
 }
 
 }  // namespace trinity
+
+namespace trinity {
+
+namespace {
+
+// Upwind voxel of (x, y, z) along direction d on the lattice; -1 if outside the box.
+long upwind_voxel(const Lattice& L, int d, const int n[3], bool periodic, const int p[3]) {
+  const int dom = L.dom[d];
+  const int sgn = L.sgn[d];
+  const int kp = sgn > 0 ? p[dom] : n[dom] - 1 - p[dom];
+  int q[3] = {p[0], p[1], p[2]};
+  q[dom] = p[dom] - sgn;
+  int j = 0;
+  for (int a = 0; a < 3; ++a) {
+    if (a == dom) continue;
+    q[a] = p[a] - L.off[(static_cast<size_t>(d) * 2 + j) * L.nmax + kp];
+    ++j;
+  }
+  if (periodic) {
+    for (int a = 0; a < 3; ++a) q[a] = ((q[a] % n[a]) + n[a]) % n[a];
+  } else {
+    if (kp == 0) return -1;
+    for (int a = 0; a < 3; ++a)
+      if (q[a] < 0 || q[a] >= n[a]) return -1;
+  }
+  return (static_cast<long>(q[2]) * n[1] + q[1]) * n[0] + q[0];
+}
+
+// Unpolarised Fresnel reflectance, cosine form 1/2 (r_s^2 + r_p^2) (= Eq. 14), with the
+// cosine of the Snell angle (Eq. 13); R = 1 under total internal reflection.
+double fresnel_reflectance(double n1, double n2, double cos1, double* cos2_out) {
+  const double eta = n1 / n2;
+  const double sin2t = eta * eta * (1.0 - cos1 * cos1);
+  if (cos1 <= 0.0 || sin2t >= 1.0) {
+    *cos2_out = 0.0;
+    return 1.0;
+  }
+  const double cos2 = std::sqrt(1.0 - sin2t);
+  const double rs = (n1 * cos1 - n2 * cos2) / (n1 * cos1 + n2 * cos2);
+  const double rp = (n2 * cos1 - n1 * cos2) / (n2 * cos1 + n1 * cos2);
+  *cos2_out = cos2;
+  return 0.5 * (rs * rs + rp * rp);
+}
+
+int nearest_pixel(const std::vector<double>& dirs, const double v[3]) {
+  const int na = static_cast<int>(dirs.size() / 3);
+  double best = -3.0;
+  std::vector<double> dots(na);
+  for (int d = 0; d < na; ++d) {
+    dots[d] = dirs[3 * d] * v[0] + dirs[3 * d + 1] * v[1] + dirs[3 * d + 2] * v[2];
+    best = std::max(best, dots[d]);
+  }
+  for (int d = 0; d < na; ++d)
+    if (dots[d] >= best - 1e-12) return d;
+  return 0;
+}
+
+// d(n)/d(axis) at index i of a line of length len (central inside, one-sided at ends).
+double grad1(const std::vector<float>& nm, long base, long stride, int i, int len, double h) {
+  if (len < 2) return 0.0;
+  if (i == 0) return (double(nm[base + stride]) - double(nm[base])) / h;
+  if (i == len - 1) return (double(nm[base + i * stride]) - double(nm[base + (i - 1) * stride])) / h;
+  return (double(nm[base + (i + 1) * stride]) - double(nm[base + (i - 1) * stride])) / (2.0 * h);
+}
+
+}  // namespace
+
+InterfaceTable build_interfaces(const std::vector<double>& dirs, const Lattice& L, int nx, int ny,
+                                int nz, double h, bool periodic, const std::vector<float>& nmap) {
+  InterfaceTable T;
+  const int na = static_cast<int>(dirs.size() / 3);
+  T.na = na;
+  const int n[3] = {nx, ny, nz};
+  const long nv = static_cast<long>(nx) * ny * nz;
+  // candidates: voxels with a different n anywhere in their 3x3x3 neighbourhood
+  std::vector<long> cand;
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const long v = (static_cast<long>(z) * ny + y) * nx + x;
+        bool diff = false;
+        for (int dz = -1; dz <= 1 && !diff; ++dz)
+          for (int dy = -1; dy <= 1 && !diff; ++dy)
+            for (int dx = -1; dx <= 1 && !diff; ++dx) {
+              int qx = x + dx, qy = y + dy, qz = z + dz;
+              if (periodic) {
+                qx = (qx + nx) % nx;
+                qy = (qy + ny) % ny;
+                qz = (qz + nz) % nz;
+              } else if (qx < 0 || qy < 0 || qz < 0 || qx >= nx || qy >= ny || qz >= nz) {
+                continue;
+              }
+              if (nmap[(static_cast<long>(qz) * ny + qy) * nx + qx] != nmap[v]) diff = true;
+            }
+        if (diff) cand.push_back(v);
+      }
+  (void)nv;
+  for (long v : cand) {
+    const int x = static_cast<int>(v % nx), y = static_cast<int>((v / nx) % ny), z = static_cast<int>(v / (static_cast<long>(nx) * ny));
+    const int p[3] = {x, y, z};
+    double g[3];
+    g[0] = grad1(nmap, (static_cast<long>(z) * ny + y) * nx, 1, x, nx, h);
+    g[1] = grad1(nmap, static_cast<long>(z) * ny * nx + x, nx, y, ny, h);
+    g[2] = grad1(nmap, static_cast<long>(y) * nx + x, static_cast<long>(nx) * ny, z, nz, h);
+    const double gn = std::sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    if (gn == 0.0) continue;
+    const double m[3] = {g[0] / gn, g[1] / gn, g[2] / gn};
+    std::vector<std::vector<std::pair<int, double>>> rows(na);  // gather rows
+    std::vector<uint8_t> keep(na, 1);
+    bool any = false;
+    for (int j = 0; j < na; ++j) {
+      const long u = upwind_voxel(L, j, n, periodic, p);
+      if (u < 0 || nmap[u] == nmap[v]) continue;
+      const double n1 = nmap[u], n2 = nmap[v];
+      const double om[3] = {dirs[3 * j], dirs[3 * j + 1], dirs[3 * j + 2]};
+      const double dn = om[0] * m[0] + om[1] * m[1] + om[2] * m[2];
+      const double cos1 = std::fabs(dn);
+      double cos2 = 0.0;
+      const double R = fresnel_reflectance(n1, n2, cos1, &cos2);
+      const double omr[3] = {om[0] - 2.0 * dn * m[0], om[1] - 2.0 * dn * m[1], om[2] - 2.0 * dn * m[2]};
+      const int dr = nearest_pixel(dirs, omr);
+      std::vector<std::pair<int, double>> outs = {{dr, R}};
+      if (R < 1.0) {
+        const double eta = n1 / n2;
+        const double s = dn >= 0 ? 1.0 : -1.0;
+        const double omt[3] = {eta * om[0] + (cos2 - eta * cos1) * s * m[0],
+                               eta * om[1] + (cos2 - eta * cos1) * s * m[1],
+                               eta * om[2] + (cos2 - eta * cos1) * s * m[2]};
+        outs.push_back({nearest_pixel(dirs, omt), 1.0 - R});
+      }
+      keep[j] = 0;
+      any = true;
+      for (const auto& o : outs) {
+        rows[o.first].push_back({j, o.second});
+        T.s_vox.push_back(static_cast<int>(v));
+        T.s_j.push_back(j);
+        T.s_d.push_back(o.first);
+        T.s_w.push_back(o.second);
+      }
+    }
+    if (!any) continue;
+    T.vox.push_back(static_cast<int>(v));
+    const int base = static_cast<int>(T.src.size());
+    int cnt = 0;
+    for (int d = 0; d < na; ++d) {
+      T.rowptr.push_back(base + cnt);
+      std::sort(rows[d].begin(), rows[d].end());
+      for (const auto& e : rows[d]) {
+        T.src.push_back(e.first);
+        T.w64.push_back(e.second);
+        T.w.push_back(static_cast<float>(e.second));
+        ++cnt;
+      }
+    }
+    T.rowptr.push_back(base + cnt);
+    T.keep.insert(T.keep.end(), keep.begin(), keep.end());
+  }
+  return T;
+}
+
+}  // namespace trinity

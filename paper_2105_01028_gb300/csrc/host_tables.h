@@ -38,3 +38,28 @@ std::vector<double> cone_weights(const std::vector<double>& dirs, int face,
 long floor_snap(double y);
 
 }  // namespace trinity
+
+namespace trinity {
+
+// Refraction / reflection at index steps (Eqs. 13-14), gather form per interface voxel:
+// out[d] = keep[d] * Q[d] + sum over entries (src j, weight w) of row d of w * Q[j].
+struct InterfaceTable {
+  int na = 0;
+  std::vector<int> vox;        // interface voxels (ascending)
+  std::vector<int> rowptr;     // [vox.size()][na + 1] entry ranges per output direction
+  std::vector<int> src;        // source direction j of each entry
+  std::vector<float> w;        // weight of each entry (FP32 copy)
+  std::vector<double> w64;     // weight of each entry (FP64)
+  std::vector<uint8_t> keep;   // [vox.size()][na] 1 if direction d does not cross
+  // scatter form (for inspection): (voxel, crossing j, target d, weight), sorted
+  std::vector<int> s_vox, s_j, s_d;
+  std::vector<double> s_w;
+};
+
+// Voxels whose upwind sample (ray lattice) lies in a voxel of different n: the arriving
+// light along that direction is split into the specular and Snell directions (each
+// snapped to the nearest pixel) with the Fresnel reflectance of Eq. 14.
+InterfaceTable build_interfaces(const std::vector<double>& dirs, const Lattice& L, int nx, int ny,
+                                int nz, double h, bool periodic, const std::vector<float>& nmap);
+
+}  // namespace trinity

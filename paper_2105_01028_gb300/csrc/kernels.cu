@@ -412,6 +412,35 @@ __global__ void __launch_bounds__(256) tally_kernel(GridParams g, const DirInfo*
 
 __global__ void advance_kernel(RunState rs) { *rs.step += 1; }
 
+// ----------------------------------------------------------------------------------------
+// Index interfaces (Eqs. 13-14): at each interface voxel the light arriving through an
+// index step is split into its specular and Snell directions.  Gather form, one warp per
+// voxel: the warp stages the voxel's Q column in shared memory, then each lane forms its
+// output directions as keep[d] Q[d] + sum_e w_e Q[src_e] in a fixed order.
+// ----------------------------------------------------------------------------------------
+constexpr int kIfaceWarps = 4;
+
+__global__ void __launch_bounds__(32 * kIfaceWarps)
+    interface_kernel(int nvox, int na, const int* __restrict__ vox, const int* __restrict__ rowptr,
+                     const int* __restrict__ src, const float* __restrict__ w,
+                     const uint8_t* __restrict__ keep, float* __restrict__ Q, size_t plane) {
+  extern __shared__ float qs[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kIfaceWarps + warp;
+  if (i >= nvox) return;  // whole warp
+  float* q = qs + warp * na;
+  const size_t v = static_cast<size_t>(vox[i]);
+  for (int d = lane; d < na; d += 32) q[d] = Q[static_cast<size_t>(d) * plane + v];
+  __syncwarp();
+  const int* rp = rowptr + static_cast<size_t>(i) * (na + 1);
+  const uint8_t* kp = keep + static_cast<size_t>(i) * na;
+  for (int d = lane; d < na; d += 32) {
+    float out = kp[d] ? q[d] : 0.0f;
+    for (int e = rp[d]; e < rp[d + 1]; ++e) out = fmaf(w[e], q[src[e]], out);
+    Q[static_cast<size_t>(d) * plane + v] = out;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_sweep(const GridParams& g, const DirInfo* dirs, const int8_t* offs,
@@ -459,6 +488,15 @@ cudaError_t launch_tally(const GridParams& g, const DirInfo* dirs, const float* 
   dim3 grid(bx, 7);
   tally_kernel<<<grid, 256, 0, st>>>(g, dirs, Iring, det_vox, det_dir, det_w, det_id,
                                      n_det_entries, det, nbins, rs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_interface(int nvox, int na, const int* vox, const int* rowptr, const int* src,
+                             const float* w, const uint8_t* keep, float* Q, int nv, cudaStream_t st) {
+  if (nvox == 0) return cudaSuccess;
+  const int blocks = (nvox + kIfaceWarps - 1) / kIfaceWarps;
+  interface_kernel<<<blocks, 32 * kIfaceWarps, kIfaceWarps * na * sizeof(float), st>>>(
+      nvox, na, vox, rowptr, src, w, keep, Q, static_cast<size_t>(nv));
   return cudaGetLastError();
 }
 

@@ -522,15 +522,15 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         }
       }
       n_active = __syncthreads_count(still);
-      // write out the voxels that stopped in this iteration: I = Q + b1 S, S.  The
-      // addresses derive from a volatile shared copy of the plane size so the compiler
-      // cannot hoist 2 x HALF 64-bit addresses out of the iteration loop into registers.
+      // write out the voxels that stopped in this iteration: I = Q + b1 S, S (Q from
+      // registers: no global load on this path).  The addresses derive from a volatile
+      // shared copy of the plane size so the compiler cannot hoist 2 x HALF 64-bit
+      // addresses out of the iteration loop into registers.
       const bool mine = newly_s[row] != 0;
       if (__any_sync(0xffffffffu, mine)) {  // warp-uniform: the TMEM loads are collective
         const size_t pl = static_cast<size_t>(*reinterpret_cast<volatile const int*>(&plane_s));
         float* pI = Iring + cur_base + static_cast<size_t>(cb) * pl + v;
         float* pS = Sring + cur_base + static_cast<size_t>(cb) * pl + v;
-        const float* pQ = Q + static_cast<size_t>(cb) * pl + v;
         float esum_row = 0.0f;
 #pragma unroll
         for (int ch = 0; ch < C::NCH; ++ch) {
@@ -541,7 +541,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 #pragma unroll
           for (int j = 0; j < C::CH; ++j) {
             if (mine) {
-              const float Iv = fmaf(vb1t[vCls[c0 + j] * kM + row], so[j], __ldg(pQ));
+              const float Iv = fmaf(vb1t[vCls[c0 + j] * kM + row], so[j], q[ch * C::CH + j]);
               *pI = Iv;
               *pS = so[j];
               esum_row += Iv;
@@ -549,7 +549,6 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
             }
             pI += pl;
             pS += pl;
-            pQ += pl;
           }
         }
         if (mine) esum += static_cast<double>(esum_row) * static_cast<double>(nidx[v]);

@@ -87,3 +87,28 @@ def test_lattice_matches_oracle_exactly(nside, shape_xyz, periodic):
 def test_cone_weights_match_oracle_exactly(nside, face, inward):
     a = T.cone_weights(nside, face, 15.0, inward)
     np.testing.assert_array_equal(a, cone_fractions(ring_directions(nside), face, 15.0, inward))
+
+
+@pytest.mark.parametrize("nside,scale,dims", [(2, 0.25, (32, 32, 12)), (4, 0.25, (24, 28, 10))])
+def test_interface_table_matches_oracle(nside, scale, dims):
+    """The library's FP64 interface split (voxel, j, d, weight) equals the oracle's."""
+    import workloads as W
+    from oracle.solver import Model
+    nx, ny, nz = dims
+    p = W.config_hetero(steps=1, precision="fp32", nx=nx, ny=ny, nz=nz, nside=nside, scale=scale)
+    m = Model(p)
+    ref = {}
+    for v, cols in m.interfaces.items():
+        for j, outs in cols.items():
+            for d, wgt in outs:
+                ref[(v, j, d)] = ref.get((v, j, d), 0.0) + wgt
+    vox, jj, dd, ww = T.interface_entries(nside, p["nidx"])
+    got = {}
+    for v, j, d, wgt in zip(vox, jj, dd, ww):
+        got[(int(v), int(j), int(d))] = got.get((int(v), int(j), int(d)), 0.0) + float(wgt)
+    ref = {k: x for k, x in ref.items() if x != 0.0}
+    got = {k: x for k, x in got.items() if x != 0.0}
+    assert len(ref) > 0
+    assert set(got) == set(ref)
+    for k in ref:
+        assert abs(got[k] - ref[k]) <= 1e-13

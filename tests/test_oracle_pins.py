@@ -353,3 +353,67 @@ def test_vacuum_budget_closes():
     r = Solver(p).run(40)
     budget = r["energy"] + np.cumsum(r["escaped"])
     assert np.mean(budget[10:30]) == pytest.approx(1.0, rel=1e-2)
+
+
+# ---------------------------------------------------------------- Fresnel / Snell (Eqs. 13-14)
+
+from oracle.fresnel import fresnel_R, fresnel_R_eq14, reflect_refract, apply_interfaces
+
+
+def test_fresnel_normal_incidence_and_critical_angle():
+    """Textbook limits: R(0) = ((n1-n2)/(n1+n2))^2 (0.027778 for 1.4 -> 1.0); total
+    reflection from the critical angle asin(n2/n1) = 45.585 deg on."""
+    assert fresnel_R(1.4, 1.0, 1.0) == pytest.approx((0.4 / 2.4) ** 2, rel=1e-14)
+    assert fresnel_R(1.0, 1.4, 1.0) == pytest.approx((0.4 / 2.4) ** 2, rel=1e-14)
+    tc = np.arcsin(1.0 / 1.4)
+    assert np.degrees(tc) == pytest.approx(45.585, abs=1e-3)
+    assert fresnel_R(1.4, 1.0, np.cos(tc + 1e-6)) == 1.0
+    assert fresnel_R(1.4, 1.0, np.cos(tc - 1e-3)) < 1.0
+    assert fresnel_R(1.0, 1.4, 1e-9) == pytest.approx(1.0, abs=1e-6)  # grazing
+
+
+@pytest.mark.parametrize("n1,n2", [(1.4, 1.0), (1.0, 1.4), (1.51, 1.33)])
+def test_fresnel_matches_eq14_form(n1, n2):
+    """The cosine form used by the solver equals Eq. 14 as printed (sin/tan form)."""
+    tmax = np.arcsin(min(1.0, n2 / n1)) - 1e-3 if n1 > n2 else np.pi / 2 - 1e-3
+    th = np.linspace(1e-3, tmax, 50)
+    np.testing.assert_allclose(fresnel_R(n1, n2, np.cos(th)), fresnel_R_eq14(n1, n2, th), rtol=1e-10)
+
+
+def test_snell_direction():
+    """Transmitted direction: unit length, in the plane of incidence, n1 sin1 = n2 sin2."""
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        om = rng.normal(size=3); om /= np.linalg.norm(om)
+        m = rng.normal(size=3); m /= np.linalg.norm(m)
+        n1, n2 = 1.0, 1.4
+        R, om_r, om_t = reflect_refract(om, m, n1, n2)
+        assert np.linalg.norm(om_r) == pytest.approx(1.0, abs=1e-12)
+        assert np.dot(om_r, m) == pytest.approx(-np.dot(om, m), abs=1e-12)
+        assert np.linalg.norm(om_t) == pytest.approx(1.0, abs=1e-12)
+        assert np.dot(np.cross(om, m), om_t) == pytest.approx(0.0, abs=1e-12)
+        s1 = np.linalg.norm(np.cross(om, m))
+        s2 = np.linalg.norm(np.cross(om_t, m))
+        assert n1 * s1 == pytest.approx(n2 * s2, abs=1e-12)
+        assert np.sign(np.dot(om_t, m)) == np.sign(np.dot(om, m))
+
+
+def test_interface_redistribution_conserves_photons():
+    """The interface operator is column-stochastic: the sum over directions of Q at every
+    interface voxel is unchanged, and it moves intensity only where n changes."""
+    p = W.config_hetero(steps=1, precision="fp32", nx=24, ny=24, nz=8, nside=2, scale=0.25)
+    m = Model(p)
+    assert len(m.interfaces) > 0
+    rng = np.random.default_rng(0)
+    Q = rng.uniform(0, 1, (m.na, m.nv))
+    Q2 = apply_interfaces(m.interfaces, Q.copy())
+    np.testing.assert_allclose(Q2.sum(axis=0), Q.sum(axis=0), rtol=1e-13)
+    moved = np.nonzero(np.abs(Q2 - Q).max(axis=0) > 0)[0]
+    assert set(moved) <= set(m.interfaces.keys())
+    n = m.nidx
+    for v in m.interfaces:
+        z, rem = divmod(v, p["nx"] * p["ny"])
+        y, x = divmod(rem, p["nx"])
+        nb = [n[v + o] for o, ok in ((1, x + 1 < p["nx"]), (-1, x > 0), (p["nx"], y + 1 < p["ny"]),
+                                        (-p["nx"], y > 0)) if ok]
+        assert any(b != n[v] for b in nb)

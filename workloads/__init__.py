@@ -110,6 +110,7 @@ def config_hetero(steps=1500, precision="bf16", tol=1e-6, nx=128, ny=128, nz=96,
     nidx[cyl] = 1.0
     p["mua"], p["mus"], p["nidx"] = (a.astype(np.float32) for a in (mua, mus, nidx))
     p["spheres"] = [(tuple(map(float, c)), float(r), float(f)) for c, r, f in spheres]
+    p["fresnel"] = True  # refraction and reflection at the cylinder wall
     p["cylinder"] = dict(axis=2, center=(cx, cy), radius=rc)
     cu, cv = float(ny // 2), float(nz // 2)
     p["source"] = dict(face=0, u_mm=cu, v_mm=cv, half_angle_deg=15.0, pulse_steps=1, energy=1.0)
