@@ -54,6 +54,28 @@ def peaks():
         return p
 
 
+def measured_traffic(kernel, updates):
+    """DRAM bytes of one launch of ``kernel`` from the committed ncu table, scaled to
+    ``updates`` (traffic grows in proportion to the updates a launch processes), or None
+    when the kernel's source has changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    for ln in lines:
+        parts = ln.split()
+        if len(parts) >= 4 and not ln.startswith("#") and parts[0] == kernel:
+            src = os.path.join(ROOT, "paper_2105_01028_gb300", "csrc", parts[1])
+            try:
+                sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:len(parts[2])]
+            except OSError:
+                return None
+            return float(parts[3]) * updates if sha == parts[2] else None
+    return None
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -187,6 +209,59 @@ def workload_config(args):
             "precision": args.precision}
 
 
+def run_serve(args):
+    """Served stream (a bounded sample of the served workload): Poisson arrivals, cubic
+    grids drawn from 32..64 voxels (the full stream draws 32..96), 48 or 192 directions,
+    100..300 steps (the full stream draws 500..1500), log-normal random-field optics.
+    Requests are submitted at their arrival times; reports solves/s over the makespan,
+    p50/p99 latency (submission to detector curves on the host), aggregate updates/s
+    and the largest number of concurrent solves."""
+    import torch
+    import paper_2105_01028_gb300 as T
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(4)
+    reqs = []
+    t = 0.0
+    for k in range(args.serve):
+        t += rng.exponential(1.0 / args.rate)
+        n = int(rng.integers(32, 65))
+        ns = 2 if rng.random() < 0.5 else 4
+        steps = int(rng.integers(100, 301))
+        reqs.append((t, W.config_served(n, ns, steps, seed=1000 + k, precision=args.precision)))
+    free, total = torch.cuda.mem_get_info()
+    srv = T.Server(hbm_budget_bytes=int(0.8 * free), max_slots=args.slots, steps_per_slice=32)
+    # warm-up: one small request (first-use costs of the library and the device)
+    wid = srv.submit(W.config_served(16, 2, 10, seed=1, precision=args.precision))
+    srv.wait(wid)
+    ids = []
+    t0 = time.perf_counter()
+    for at, p in reqs:
+        dt = at - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        ids.append(srv.submit(p))
+    lat = []
+    for rid in ids:
+        st, rc, det, ms = srv.wait(rid, timeout_s=3600)
+        if st != T.REQ_DONE:
+            raise RuntimeError("request %d ended in state %d (status %d)" % (rid, st, rc))
+        lat.append(ms)
+    span = time.perf_counter() - t0
+    updates = sum(p["nx"] * p["ny"] * p["nz"] * 12 * p["nside"] ** 2 * p["steps"] for _, p in reqs)
+    stats = srv.stats()
+    srv.close()
+    line = {"metric": "served solves/s", "value": len(reqs) / span, "unit": "solves/s", "n_gpus": 1,
+            "higher_is_better": True, "precision": args.precision, "data": "synthetic",
+            "config": {"workload": "served stream sample: %d requests, Poisson arrivals at %.1f/s, cubic "
+                                   "32..64 voxels, 48/192 dirs, 100..300 steps, log-normal GRF optics"
+                                   % (len(reqs), args.rate), "slots": args.slots},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(np.max(lat))},
+            "updates_per_s": updates / span, "makespan_s": span,
+            "max_concurrent": stats["max_concurrent"], "completed": stats["completed"]}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -204,11 +279,18 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--grid", type=int, nargs=3, default=[96, 96, 64], metavar=("NX", "NY", "NZ"),
                     help="slab size (smaller grids are for profiling captures only)")
+    ap.add_argument("--serve", type=int, default=0, metavar="N",
+                    help="run the served stream with N requests instead of the slab")
+    ap.add_argument("--rate", type=float, default=8.0, help="served stream arrival rate (1/s)")
+    ap.add_argument("--slots", type=int, default=8, help="served stream concurrent slots")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.serve:
+        run_serve(args)
         return
 
     import torch
@@ -294,8 +376,9 @@ def main():
         {"name": "tally+advance", "ms": per[2], "share": per[2] / tot},
     ]
     dom = max(kernels[:2], key=lambda k: k["ms"])
+    traffic = measured_traffic("scatter_tc_kernel", nv * na) if dom["name"] == "scatter_bf16" else None
     roof = {"kernel": dom["name"], "bound": dom["bound"], "achieved": dom["achieved"],
-            "peak": dom["peak"], "unit": dom["unit"], "frac": dom["frac"], "traffic": None,
+            "peak": dom["peak"], "unit": dom["unit"], "frac": dom["frac"], "traffic": traffic,
             "peak_source": pk["_source"] + (" (FP32 FFMA: 152 SMs x 128 lanes x 2 x max SM clock)"
                                             if dom["bound"] == "alu" else "")}
 

@@ -187,6 +187,79 @@ void trinity_destroy(trinity_ctx* ctx);
  * layouts, descriptors and TMEM read-out as the iteration kernel.  For testing. */
 int trinity_tc_selftest(int na, const uint16_t* A, const uint16_t* B, float* D);
 
+/* ---- Serving: many forward solves at once on one GPU. ----
+ *
+ * Reconstruction needs many forward models.  A server queues solve requests and admits
+ * them, in arrival order, into slots while their device footprint
+ * (trinity_footprint_bytes) fits the budget and a slot is free.  Each admitted request
+ * runs in its own context on its own CUDA stream; a worker thread advances all active
+ * requests round-robin in slices of graph-replayed steps, so their kernels overlap on the
+ * device, and returns the detector curves and the latency (submission to completion).
+ * Results do not depend on what else is running.  All CUDA work happens on the worker
+ * thread of the server (on the device current when the first request is submitted). */
+typedef struct trinity_server trinity_server;
+
+typedef struct {
+  int face;              /* 0..5; pulse_steps = 0 means no source */
+  double u_mm, v_mm;
+  double half_angle_deg;
+  int pulse_steps;
+  double energy;
+} trinity_source_desc;
+
+typedef struct {
+  int face;
+  double u_mm, v_mm, radius_mm, half_angle_deg;
+} trinity_detector_desc;
+
+typedef struct {
+  trinity_grid_desc grid;
+  const float *mua, *mus, *n; /* host, [nz][ny][nx]; copied at submission */
+  double g;
+  trinity_source_desc source;
+  int n_detectors;
+  const trinity_detector_desc* detectors; /* copied at submission */
+  double bin_ps;
+  int nbins;
+  int nsteps;
+  int fresnel; /* 1: refraction / reflection at index steps (trinity_set_fresnel) */
+} trinity_request;
+
+/* States reported by trinity_serve_poll. */
+enum { TRINITY_REQ_QUEUED = 0, TRINITY_REQ_ACTIVE = 1, TRINITY_REQ_DONE = 2, TRINITY_REQ_FAILED = 3,
+       TRINITY_REQ_CANCELLED = 4 };
+
+/* A server with a device-memory budget (bytes), at most ``max_slots`` concurrent solves,
+ * advancing each by ``steps_per_slice`` steps per turn. */
+int trinity_serve_create(size_t hbm_budget_bytes, int max_slots, int steps_per_slice,
+                         trinity_server** out);
+
+/* Queue a request (inputs are copied); *req_id receives its id.  TRINITY_E_OOM if its
+ * footprint exceeds the whole budget, TRINITY_E_INVALID for a malformed request.
+ * Other failures (device errors, invalid optics) surface through trinity_serve_poll. */
+int trinity_serve_submit(trinity_server* srv, const trinity_request* req, uint64_t* req_id);
+
+/* Non-blocking: *state receives TRINITY_REQ_*; once done, the detector curves
+ * ([n_detectors][nbins], n must match; may be NULL) and the latency in ms are written.
+ * Returns the request's final status once it has one. */
+int trinity_serve_poll(trinity_server* srv, uint64_t req_id, int* state, double* detectors,
+                       size_t n, double* latency_ms);
+
+/* Block until the request is done, failed or cancelled, or ``timeout_s`` passes
+ * (TRINITY_E_TIMEOUT). */
+int trinity_serve_wait(trinity_server* srv, uint64_t req_id, double timeout_s);
+
+/* Cancel a queued or running request (a running one stops at its next slice). */
+int trinity_serve_cancel(trinity_server* srv, uint64_t req_id);
+
+/* Completed and failed counts, the largest number of concurrent solves seen, and the
+ * device bytes currently held by admitted requests. */
+int trinity_serve_stats(trinity_server* srv, uint64_t* completed, uint64_t* failed,
+                        int* max_concurrent, size_t* bytes_in_use);
+
+/* Cancel everything still queued or running, join the worker and free the server. */
+void trinity_serve_destroy(trinity_server* srv);
+
 /* ---- Host-side tables (no GPU needed): the same FP64 tables the context builds. ---- */
 
 /* HEALPix RING pixel centres as unit vectors, out[N_a][3] (Section 2.1). */

@@ -17,7 +17,7 @@ FIELD_I, FIELD_S = 0, 1
 _PREC = {"fp32": FP32, "bf16": BF16}
 _BOUND = {"vacuum": 0, "periodic": 1}
 
-__all__ = ["Forward", "TrinityError", "grid_desc", "footprint_bytes", "healpix_dirs",
+__all__ = ["Forward", "Server", "TrinityError", "grid_desc", "footprint_bytes", "healpix_dirs",
            "phase_matrix", "lattice_tables", "cone_weights", "lib"]
 
 
@@ -185,6 +185,89 @@ class Forward:
         self._check(self.L.trinity_read_field(self.h, what, back, arr.ctypes.data_as(ctypes.c_void_p),
                                               arr.nbytes, 0))
         return arr
+
+
+REQ_QUEUED, REQ_ACTIVE, REQ_DONE, REQ_FAILED, REQ_CANCELLED = range(5)
+
+
+class Server:
+    """Many forward solves at once: requests are admitted by device-memory footprint into
+    slots and advanced round-robin on their own streams (see trinity_serve_* in
+    include/trinity.h)."""
+
+    def __init__(self, hbm_budget_bytes, max_slots=8, steps_per_slice=32):
+        self.L = lib()
+        h = ctypes.c_void_p()
+        rc = self.L.trinity_serve_create(int(hbm_budget_bytes), int(max_slots), int(steps_per_slice),
+                                         ctypes.byref(h))
+        if rc != OK:
+            raise TrinityError(rc, "trinity_serve_create failed")
+        self.h = h
+        self._shape = {}
+
+    def submit(self, prob):
+        """Queue a solve of ``prob`` (a problem dict, ``steps`` time steps); returns its id.
+        Raises TrinityError for malformed or over-budget requests."""
+        mua = np.ascontiguousarray(prob["mua"], dtype=np.float32)
+        mus = np.ascontiguousarray(prob["mus"], dtype=np.float32)
+        nid = np.ascontiguousarray(prob["nidx"], dtype=np.float32)
+        dets = prob.get("detectors", [])
+        darr = (_lib.DetectorDesc * max(len(dets), 1))()
+        for k, d in enumerate(dets):
+            darr[k] = _lib.DetectorDesc(int(d["face"]), float(d["u_mm"]), float(d["v_mm"]),
+                                        float(d["radius_mm"]), float(d["half_angle_deg"]))
+        src = prob.get("source")
+        sd = _lib.SourceDesc(0, 0.0, 0.0, 15.0, 0, 0.0) if src is None else _lib.SourceDesc(
+            int(src["face"]), float(src["u_mm"]), float(src["v_mm"]), float(src["half_angle_deg"]),
+            int(src["pulse_steps"]), float(src["energy"]))
+        req = _lib.Request(grid_desc(prob), mua.ctypes.data, mus.ctypes.data, nid.ctypes.data,
+                           float(prob["g"]), sd, len(dets), darr, float(prob.get("bin_ps", 10.0)),
+                           int(prob.get("nbins", 1)), int(prob["steps"]), int(bool(prob.get("fresnel", False))))
+        rid = ctypes.c_uint64()
+        rc = self.L.trinity_serve_submit(self.h, ctypes.byref(req), ctypes.byref(rid))
+        if rc != OK:
+            raise TrinityError(rc, "trinity_serve_submit rejected the request")
+        self._shape[rid.value] = (len(dets), int(prob.get("nbins", 1)))
+        return rid.value
+
+    def poll(self, rid):
+        """(state, status, detectors or None, latency_ms or None) without blocking."""
+        nd, nb = self._shape[rid]
+        det = np.zeros((nd, nb))
+        st = ctypes.c_int()
+        lat = ctypes.c_double(-1.0)
+        rc = self.L.trinity_serve_poll(self.h, rid, ctypes.byref(st), det.ctypes.data_as(_lib.P_double),
+                                       det.size, ctypes.byref(lat))
+        if st.value < REQ_DONE:
+            return st.value, rc, None, None
+        return st.value, rc, (det if st.value == REQ_DONE else None), lat.value
+
+    def wait(self, rid, timeout_s=600.0):
+        rc = self.L.trinity_serve_wait(self.h, rid, float(timeout_s))
+        if rc != OK:
+            raise TrinityError(rc, "request %d did not finish in time" % rid)
+        return self.poll(rid)
+
+    def cancel(self, rid):
+        return self.L.trinity_serve_cancel(self.h, rid)
+
+    def stats(self):
+        c, f = ctypes.c_uint64(), ctypes.c_uint64()
+        mc = ctypes.c_int()
+        used = ctypes.c_size_t()
+        self.L.trinity_serve_stats(self.h, ctypes.byref(c), ctypes.byref(f), ctypes.byref(mc), ctypes.byref(used))
+        return dict(completed=c.value, failed=f.value, max_concurrent=mc.value, bytes_in_use=used.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.trinity_serve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---- host tables (no GPU needed)

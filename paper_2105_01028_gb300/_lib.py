@@ -26,6 +26,23 @@ class GridDesc(ctypes.Structure):
                 ("max_iters", c_int)]
 
 
+class SourceDesc(ctypes.Structure):
+    _fields_ = [("face", c_int), ("u_mm", c_double), ("v_mm", c_double),
+                ("half_angle_deg", c_double), ("pulse_steps", c_int), ("energy", c_double)]
+
+
+class DetectorDesc(ctypes.Structure):
+    _fields_ = [("face", c_int), ("u_mm", c_double), ("v_mm", c_double), ("radius_mm", c_double),
+                ("half_angle_deg", c_double)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("grid", GridDesc), ("mua", c_void_p), ("mus", c_void_p), ("n", c_void_p),
+                ("g", c_double), ("source", SourceDesc), ("n_detectors", c_int),
+                ("detectors", ctypes.POINTER(DetectorDesc)), ("bin_ps", c_double),
+                ("nbins", c_int), ("nsteps", c_int), ("fresnel", c_int)]
+
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "trinity_footprint_bytes": (c_size_t, [ctypes.POINTER(GridDesc)]),
@@ -54,6 +71,14 @@ SIGNATURES = {
     "trinity_last_error": (ctypes.c_char_p, [c_void_p]),
     "trinity_destroy": (None, [c_void_p]),
     "trinity_tc_selftest": (c_int, [c_int, c_void_p, c_void_p, c_void_p]),
+    "trinity_serve_create": (c_int, [c_size_t, c_int, c_int, ctypes.POINTER(c_void_p)]),
+    "trinity_serve_submit": (c_int, [c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+    "trinity_serve_poll": (c_int, [c_void_p, ctypes.c_uint64, P_int, P_double, c_size_t, P_double]),
+    "trinity_serve_wait": (c_int, [c_void_p, ctypes.c_uint64, c_double]),
+    "trinity_serve_cancel": (c_int, [c_void_p, ctypes.c_uint64]),
+    "trinity_serve_stats": (c_int, [c_void_p, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                    P_int, ctypes.POINTER(c_size_t)]),
+    "trinity_serve_destroy": (None, [c_void_p]),
     "trinity_healpix_dirs": (c_int, [c_int, P_double, c_size_t]),
     "trinity_phase_matrix": (c_int, [c_int, c_double, P_double, c_size_t, P_double]),
     "trinity_lattice_tables": (c_int, [c_int, c_int, c_int, c_int, c_double, c_int,

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libtrinity.so")
-SOURCES = ["host_tables.cpp", "kernels.cu", "scatter_tc.cu", "api.cu"]
+SOURCES = ["host_tables.cpp", "kernels.cu", "scatter_tc.cu", "api.cu", "serve.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -48,7 +48,7 @@ def build(verbose=False, extra=()):
             if err:
                 sys.stderr.write(err)
     tmp = LIB + ".tmp"
-    cmd = [nvcc(), "-shared", *ARCH, "-o", tmp, *objs, "-lcudart_static"]
+    cmd = [nvcc(), "-shared", *ARCH, "-o", tmp, *objs, "-lcudart_static", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
