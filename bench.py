@@ -368,7 +368,7 @@ def main():
     kernels = [
         {"name": "sweep", "ms": per[0], "share": per[0] / tot, "bound": "hbm",
          "achieved": w_ach, "peak": hbm, "unit": "GB/s", "frac": w_ach / hbm,
-         "algorithmic_bytes": sweep_bytes},
+         "algorithmic_bytes": sweep_bytes, "traffic": measured_traffic("sweep_kernel", nv * na)},
         {"name": "scatter_" + args.precision, "ms": per[1], "share": per[1] / tot,
          "bound": s_bound, "achieved": s_ach, "peak": s_peak, "unit": s_unit,
          "frac": s_ach / s_peak, "algorithmic_flops": scat_flops,

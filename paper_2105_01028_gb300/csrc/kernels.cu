@@ -16,12 +16,15 @@ __device__ __forceinline__ int pick(int axis, int x, int y, int z) {
 
 // ----------------------------------------------------------------------------------------
 // Sweep: Q(v, d) = I_up exp(-x) + S_up b0(x), the known part of Eq. 10 at time level n.
-// One thread per (voxel, direction); blockIdx.y = direction, threads run along x so the
-// loads of the upwind plane (shifted by at most one voxel) coalesce.
 // The upwind sample of v is the previous point of its long ray (slab lattice, Section
 // 2.1): one slab back along dom(d), shifted by the per-slab offsets.  Its I and S are
 // taken at the retarded time n - delta, delta = ds n(v) / (c0 dt), linearly
 // interpolated between the stored levels n - m and n - m - 1 (m = floor(delta)).
+//
+// Mapping: blockIdx.y = direction; a block covers whole x-rows (threadIdx.x along x,
+// threadIdx.y one row each), so a warp reads contiguous, at most one-voxel-shifted runs
+// of the upwind plane.  The direction's constants are staged in shared memory once per
+// block, and the lattice offsets are uniform along a row unless x is the dominant axis.
 // ----------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) sweep_kernel(GridParams g, const DirInfo* __restrict__ dirs,
                                                     const int8_t* __restrict__ offs,
@@ -30,33 +33,43 @@ __global__ void __launch_bounds__(256) sweep_kernel(GridParams g, const DirInfo*
                                                     const float* __restrict__ mut,
                                                     const float* __restrict__ nidx,
                                                     float* __restrict__ Q, RunState rs) {
-  const int n = *rs.step;
+  __shared__ DirInfo di_s;
+  __shared__ int n_s;
   const int d = blockIdx.y;
-  if (d == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
-    rs.smax[n & 1] = 0u;      // max |S(n)|, filled by this step's source iteration
-    rs.tile_ctr[n & 1] = 0;   // work counter of this step's persistent kernel
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    di_s = dirs[d];
+    n_s = *rs.step;
+    if (d == 0 && blockIdx.x == 0) {
+      rs.smax[n_s & 1] = 0u;     // max |S(n)|, filled by this step's source iteration
+      rs.tile_ctr[n_s & 1] = 0;  // work counter of this step's persistent kernel
+    }
   }
-  const DirInfo di = dirs[d];
+  __syncthreads();
+  const int row = blockIdx.x * blockDim.y + threadIdx.y;  // (y, z) row index
+  if (row >= g.ny * g.nz) return;
+  const int n = n_s;
+  const int dom = di_s.dom, sgn = di_s.sgn, a0 = di_s.a0, a1 = di_s.a1;
+  const float ds = di_s.ds, dc_hi = di_s.dcoef, dc_lo = di_s.dcoef_lo, src_amp = di_s.src_amp;
+  const int y = row % g.ny, z = row / g.ny;
   const size_t plane = static_cast<size_t>(g.nv);
   const int8_t* off0 = offs + (static_cast<size_t>(d) * 2 + 0) * g.nmax;
   const int8_t* off1 = offs + (static_cast<size_t>(d) * 2 + 1) * g.nmax;
-  const int nd = pick(di.dom, g.nx, g.ny, g.nz);
-  const int n0 = pick(di.a0, g.nx, g.ny, g.nz);
-  const int n1 = pick(di.a1, g.nx, g.ny, g.nz);
-  const int sd = di.dom == 0 ? 1 : (di.dom == 1 ? g.nx : g.nx * g.ny);
-  const int s0 = di.a0 == 0 ? 1 : (di.a0 == 1 ? g.nx : g.nx * g.ny);
-  const int s1 = di.a1 == 0 ? 1 : (di.a1 == 1 ? g.nx : g.nx * g.ny);
+  const int nd = pick(dom, g.nx, g.ny, g.nz);
+  const int n0 = pick(a0, g.nx, g.ny, g.nz);
+  const int n1 = pick(a1, g.nx, g.ny, g.nz);
+  const int sd = dom == 0 ? 1 : (dom == 1 ? g.nx : g.nx * g.ny);
+  const int s0 = a0 == 0 ? 1 : (a0 == 1 ? g.nx : g.nx * g.ny);
+  const int s1 = a1 == 0 ? 1 : (a1 == 1 ? g.nx : g.nx * g.ny);
+  const size_t lev0 = static_cast<size_t>(d) * plane;
+  const size_t row_base = static_cast<size_t>(row) * g.nx;
 
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < g.nv; v += gridDim.x * blockDim.x) {
-    const int x = v % g.nx;
-    const int t = v / g.nx;
-    const int y = t % g.ny;
-    const int z = t / g.ny;
-    const int pd = pick(di.dom, x, y, z);
-    const int p0 = pick(di.a0, x, y, z);
-    const int p1 = pick(di.a1, x, y, z);
-    const int kp = di.sgn > 0 ? pd : nd - 1 - pd;
-    int qd = pd - di.sgn;
+  for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
+    const size_t v = row_base + x;
+    const int pd = pick(dom, x, y, z);
+    const int p0 = pick(a0, x, y, z);
+    const int p1 = pick(a1, x, y, z);
+    const int kp = sgn > 0 ? pd : nd - 1 - pd;
+    int qd = pd - sgn;
     int q0 = p0 - off0[kp];
     int q1 = p1 - off1[kp];
     int kind = 0;  // 0: upwind inside, 1: inflow face, 2: entered through a side face
@@ -71,7 +84,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(GridParams g, const DirInfo*
     }
     int m;
     float f;
-    retarded_delay(di.dcoef, di.dcoef_lo, nidx[v], m, f);
+    retarded_delay(dc_hi, dc_lo, __ldg(nidx + v), m, f);
     const int L0 = n - m, L1 = n - m - 1;
     float Iup = 0.0f, Sup = 0.0f;
     if (kind == 0) {
@@ -79,25 +92,25 @@ __global__ void __launch_bounds__(256) sweep_kernel(GridParams g, const DirInfo*
                        static_cast<size_t>(q1) * s1;
       float i0 = 0.0f, i1 = 0.0f, s0v = 0.0f, s1v = 0.0f;
       if (L0 >= g.hist_from) {
-        const size_t o = (static_cast<size_t>(ring_slot(L0)) * g.na + d) * plane + u;
+        const size_t o = static_cast<size_t>(ring_slot(L0)) * g.na * plane + lev0 + u;
         i0 = __ldg(Iring + o);
         s0v = __ldg(Sring + o);
       }
       if (L1 >= g.hist_from) {
-        const size_t o = (static_cast<size_t>(ring_slot(L1)) * g.na + d) * plane + u;
+        const size_t o = static_cast<size_t>(ring_slot(L1)) * g.na * plane + lev0 + u;
         i1 = __ldg(Iring + o);
         s1v = __ldg(Sring + o);
       }
       Iup = (1.0f - f) * i0 + f * i1;
       Sup = (1.0f - f) * s0v + f * s1v;
-    } else if (kind == 1 && v == g.src_voxel && di.src_amp != 0.0f) {
+    } else if (kind == 1 && static_cast<int>(v) == g.src_voxel && src_amp != 0.0f) {
       const float on0 = (L0 >= 0 && L0 < g.pulse_steps) ? 1.0f : 0.0f;
       const float on1 = (L1 >= 0 && L1 < g.pulse_steps) ? 1.0f : 0.0f;
-      Iup = di.src_amp * ((1.0f - f) * on0 + f * on1);
+      Iup = src_amp * ((1.0f - f) * on0 + f * on1);
     }
-    const float xo = mut[v] * di.ds;
+    const float xo = __ldg(mut + v) * ds;
     const float T = expf(-xo);
-    Q[static_cast<size_t>(d) * plane + v] = Iup * T + Sup * ray_b0(xo, T);
+    Q[lev0 + v] = Iup * T + Sup * ray_b0(xo, T);
   }
 }
 
@@ -446,10 +459,13 @@ __global__ void __launch_bounds__(32 * kIfaceWarps)
 cudaError_t launch_sweep(const GridParams& g, const DirInfo* dirs, const int8_t* offs,
                          const float* Iring, const float* Sring, const float* mut,
                          const float* nidx, float* Q, RunState rs, cudaStream_t st) {
-  const int threads = 256;
-  const int bx = (g.nv + threads - 1) / threads;
-  dim3 grid(bx, g.na);
-  sweep_kernel<<<grid, threads, 0, st>>>(g, dirs, offs, Iring, Sring, mut, nidx, Q, rs);
+  int bx = ((g.nx + 31) / 32) * 32;
+  if (bx > 256) bx = 256;
+  const int by = 256 / bx;
+  const int rows = g.ny * g.nz;
+  dim3 block(bx, by);
+  dim3 grid((rows + by - 1) / by, g.na);
+  sweep_kernel<<<grid, block, 0, st>>>(g, dirs, offs, Iring, Sring, mut, nidx, Q, rs);
   return cudaGetLastError();
 }
 

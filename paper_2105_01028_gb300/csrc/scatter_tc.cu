@@ -20,8 +20,9 @@
 // 16-byte chunk c of row r sits at chunk position c ^ (r & 7).  A = X tile (128 rows x
 // K), B = Pb (N_a rows x K), K padded to a multiple of 64 with zeros.
 // TMEM: columns [0, N_a) hold D, columns [SOFF, SOFF + N_a) hold S_old (FP32).
-// Thread mapping: 12 warps; warp w reads TMEM lanes 32 (w % 4) .. + 31 (one voxel row
-// per thread) and the column group w / 4 (a third of the directions).
+// Thread mapping: 16 warps (12 for 48 directions); warp w reads TMEM lanes 32 (w % 4) ..
+// + 31 (one voxel row per thread) and the column group w / 4 (a quarter / third of the
+// directions).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -34,8 +35,13 @@ namespace trinity {
 namespace {
 
 constexpr int kM = 128;
-constexpr int kGroups = 3;                 // column groups (warps w, w+4, w+8 share TMEM lanes)
-constexpr int kThreadsTc = 128 * kGroups;
+// Column groups: warps w, w+4, w+8, ... share the TMEM lanes of one 32-voxel quarter and
+// split the directions.  Four groups (16 warps) for 192 directions, three for 48.
+template <int NA>
+struct TcThreads {
+  static constexpr int kGroups = NA >= 192 ? 4 : 3;
+  static constexpr int kThreads = 128 * kGroups;
+};
 constexpr int kMaxClasses = 16;
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s: bound on every mbarrier wait
 
@@ -44,8 +50,10 @@ struct Tc {
   static constexpr int KP = (NA + 63) / 64 * 64;   // padded K
   static constexpr int KB = KP / 64;               // 128-byte K blocks
   static constexpr int KSTEPS = KP / 16;           // MMAs per operand (K = 16 each)
+  static constexpr int kGroups = TcThreads<NA>::kGroups;
+  static constexpr int kThreads = TcThreads<NA>::kThreads;
   static constexpr int HALF = NA / kGroups;        // columns per thread
-  static constexpr int CH = (HALF % 16 == 0) ? 16 : 8;  // TMEM load width
+  static constexpr int CH = (HALF % 16 == 0 && NA < 192) ? 16 : 8;  // TMEM load width
   static constexpr int NCH = HALF / CH;
   static_assert(HALF % 8 == 0, "column group must be a whole number of 16-byte chunks");
   static constexpr int POW2 = NA <= 64 ? 64 : (NA <= 128 ? 128 : 256);
@@ -267,7 +275,7 @@ __device__ __forceinline__ void load_b_operand(uint8_t* sB, const uint16_t* __re
 // ---------------------------------------------------------------- the iteration kernel
 
 template <int NA>
-__global__ void __launch_bounds__(kThreadsTc, 1)
+__global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
     scatter_tc_kernel(GridParams g, const float* __restrict__ rcorr, const uint8_t* __restrict__ cls,
                       const float* __restrict__ cls_ds, int ncls, const uint16_t* __restrict__ Pbf,
                       const float* __restrict__ Q, const float* __restrict__ mut, const float* __restrict__ eps,
@@ -288,10 +296,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   __shared__ int tile_s;
   __shared__ int plane_s;
   __shared__ float e_s[kM], rho_s[kM], best_s[kM];
+  constexpr int kGroups = C::kGroups;
   __shared__ float red_d[kGroups][kM], red_s[kGroups][kM];
   __shared__ int act_s[kM], newly_s[kM], stall_s[kM], iters_s[kM];
-  __shared__ double esum_s[kThreadsTc / 32];
-  __shared__ float smax_s[kThreadsTc / 32];
+  __shared__ double esum_s[C::kThreads / 32];
+  __shared__ float smax_s[C::kThreads / 32];
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -598,7 +607,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   if (tid == 0) {
     double e = 0.0;
     float sm = 0.0f;
-    for (int w = 0; w < kThreadsTc / 32; ++w) {
+    for (int w = 0; w < C::kThreads / 32; ++w) {
       e += esum_s[w];
       sm = fmaxf(sm, smax_s[w]);
     }
@@ -616,7 +625,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 // with zeros), using the same operand layouts, descriptors and TMEM read-out as the
 // iteration kernel; D [128][NA] fp32.
 template <int NA>
-__global__ void __launch_bounds__(kThreadsTc, 1)
+__global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
     tc_tile_selftest_kernel(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, float* __restrict__ D,
                             int* __restrict__ err) {
   using C = Tc<NA>;
@@ -714,10 +723,10 @@ cudaError_t launch_scatter_bf16(const GridParams& g, const BfTables& t, const ui
   const int ntiles = (g.nv + kM - 1) / kM;
   const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
   if (g.na == 48) {
-    scatter_tc_kernel<48><<<grid, kThreadsTc, Tc<48>::SMEM, st>>>(g, t.rcorr, t.cls, t.cls_ds, t.ncls, Pbf, Q, mut,
+    scatter_tc_kernel<48><<<grid, Tc<48>::kThreads, Tc<48>::SMEM, st>>>(g, t.rcorr, t.cls, t.cls_ds, t.ncls, Pbf, Q, mut,
                                                                   eps, nidx, Iring, Sring, tol, max_iters, rs);
   } else if (g.na == 192) {
-    scatter_tc_kernel<192><<<grid, kThreadsTc, Tc<192>::SMEM, st>>>(g, t.rcorr, t.cls, t.cls_ds, t.ncls, Pbf, Q,
+    scatter_tc_kernel<192><<<grid, Tc<192>::kThreads, Tc<192>::SMEM, st>>>(g, t.rcorr, t.cls, t.cls_ds, t.ncls, Pbf, Q,
                                                                     mut, eps, nidx, Iring, Sring, tol, max_iters, rs);
   } else {
     return cudaErrorInvalidValue;
@@ -728,9 +737,9 @@ cudaError_t launch_scatter_bf16(const GridParams& g, const BfTables& t, const ui
 cudaError_t tc_tile_selftest(int na, const uint16_t* A, const uint16_t* B, float* D, int* err, cudaStream_t st) {
   if (!scatter_bf16_supported(na)) return cudaErrorNotSupported;
   if (na == 48)
-    tc_tile_selftest_kernel<48><<<1, kThreadsTc, Tc<48>::SMEM, st>>>(A, B, D, err);
+    tc_tile_selftest_kernel<48><<<1, Tc<48>::kThreads, Tc<48>::SMEM, st>>>(A, B, D, err);
   else
-    tc_tile_selftest_kernel<192><<<1, kThreadsTc, Tc<192>::SMEM, st>>>(A, B, D, err);
+    tc_tile_selftest_kernel<192><<<1, Tc<192>::kThreads, Tc<192>::SMEM, st>>>(A, B, D, err);
   return cudaGetLastError();
 }
 
