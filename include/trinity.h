@@ -260,6 +260,38 @@ int trinity_serve_stats(trinity_server* srv, uint64_t* completed, uint64_t* fail
 /* Cancel everything still queued or running, join the worker and free the server. */
 void trinity_serve_destroy(trinity_server* srv);
 
+/* ---- Source iteration that allocates nothing ----
+ *
+ * The paper has no counterpart of this call; it exists for callers that cannot call
+ * cudaMalloc where they need a solve (their framework's memory pool owns the device, or
+ * the code runs where allocation is forbidden).  It runs the per-voxel source iteration
+ * S = (1 - eps) P (Q + b1 o S) of the FP32 mode (same arithmetic and stop rule as
+ * trinity_step) on caller-owned device buffers and allocates no device memory: its
+ * scratch (per-voxel contraction bounds, a max-reduction cell, iteration counters) is a
+ * static device array of 4 MiB + 16 B that every GPU loading the library holds until the
+ * process exits.
+ *   na       12, 48 or 192 directions; nvox voxels, 1 <= nvox <= 1048576 (the scratch
+ *            limit: larger sizes return TRINITY_E_INVALID without running).
+ *   P        [na][na] FP32, symmetric with unit row sums up to rounding (e.g. the matrix of
+ *            trinity_phase_matrix in FP32); the row-sum defect is corrected inside.
+ *   Q, b1    [na][nvox] FP32: the known part of Eq. 10 and the weight of S(n) in it.
+ *   eps      [nvox] FP32: mu_a / mu_t (1 where mu_t = 0).
+ *   S_prev   [na][nvox] FP32: the start of the iteration (the previous step's S).
+ *   S_out, I_out [na][nvox] FP32 outputs: S and I = Q + b1 o S.
+ *   tol, max_iters as in trinity_grid_desc; *iters_max (may be NULL) gets the largest
+ *   iteration count.  All pointers except iters_max are device pointers of the current
+ *   device; the work runs on ``stream`` (a cudaStream_t or NULL) and the call returns
+ *   after it finishes.  TRINITY_W_NOT_CONVERGED if a voxel reached max_iters.
+ * The first call on a device looks up the scratch array's device address (a host-side
+ * step, once per device); make that first call before any stream capture.  Every call
+ * shares the one array and clears the parts that must start at zero, so calls whose GPU
+ * work overlaps (concurrent streams, threads or processes sharing the library on one
+ * device) race on it and must be serialised by the caller. */
+int trinity_source_iteration_noalloc(int na, int nvox, const float* P, const float* Q,
+                                     const float* b1, const float* eps, const float* S_prev,
+                                     float* S_out, float* I_out, double tol, int max_iters,
+                                     int* iters_max, void* stream);
+
 /* ---- Host-side tables (no GPU needed): the same FP64 tables the context builds. ---- */
 
 /* HEALPix RING pixel centres as unit vectors, out[N_a][3] (Section 2.1). */

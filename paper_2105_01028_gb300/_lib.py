@@ -71,6 +71,8 @@ SIGNATURES = {
     "trinity_last_error": (ctypes.c_char_p, [c_void_p]),
     "trinity_destroy": (None, [c_void_p]),
     "trinity_tc_selftest": (c_int, [c_int, c_void_p, c_void_p, c_void_p]),
+    "trinity_source_iteration_noalloc": (c_int, [c_int, c_int] + [c_void_p] * 7 +
+                                         [c_double, c_int, P_int, c_void_p]),
     "trinity_serve_create": (c_int, [c_size_t, c_int, c_int, ctypes.POINTER(c_void_p)]),
     "trinity_serve_submit": (c_int, [c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
     "trinity_serve_poll": (c_int, [c_void_p, ctypes.c_uint64, P_int, P_double, c_size_t, P_double]),
