@@ -269,7 +269,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--spinup", type=int, default=600)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
     ap.add_argument("--compare-fp32", action="store_true",
                     help="also time the plain FP32 path on the same window")
     ap.add_argument("--cpu-voxels", type=int, default=16384,

@@ -295,10 +295,10 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
   __shared__ uint32_t tmem_base_s;
   __shared__ int tile_s;
   __shared__ int plane_s;
-  __shared__ float e_s[kM], rho_s[kM], best_s[kM];
+  __shared__ int abort_s;
+  __shared__ float e_s[kM], rho_s[kM];
   constexpr int kGroups = C::kGroups;
-  __shared__ float red_d[kGroups][kM], red_s[kGroups][kM];
-  __shared__ int act_s[kM], newly_s[kM], stall_s[kM], iters_s[kM];
+  __shared__ float red_d[2][kGroups][kM], red_s[2][kGroups][kM];  // by iteration parity
   __shared__ double esum_s[C::kThreads / 32];
   __shared__ float smax_s[C::kThreads / 32];
 
@@ -320,6 +320,7 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
   if (tid == 0) {
     mbar_init(&mbar);
     plane_s = g.nv;
+    abort_s = 0;
   }
   load_b_operand<NA>(sB, Pbf);
   for (int i = tid; i < NA; i += blockDim.x) {
@@ -369,11 +370,6 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
       }
       e_s[tid] = ev;
       rho_s[tid] = rho;
-      best_s[tid] = 3.0e38f;
-      stall_s[tid] = 0;
-      iters_s[tid] = 0;
-      act_s[tid] = vv < g.nv ? 1 : 0;
-      newly_s[tid] = 0;
     }
     for (int u = tid; u < ncls * kM; u += blockDim.x) {
       const int k = u / kM, r = u % kM;
@@ -424,19 +420,21 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
       mma_commit(&mbar);
     }
 
+    // Per-row iteration state lives in registers: the kGroups threads that share a voxel
+    // row read the same reduced values and so take the same decisions.
+    bool act = vin;
+    float best = 3.0e38f;
+    int stall = 0, iters = 0;
+    const float ev = e_s[row];
+    const float rho = rho_s[row];
     int k = 0;
-    int n_active = 1;
     while (true) {
       ++k;
       const bool ok = mbar_wait_bounded(&mbar, phase);
       phase ^= 1u;
-      if (__syncthreads_or(!ok)) {
-        aborted = true;
-        break;
-      }
+      if (!ok) abort_s = 1;
+      const bool to = __any_sync(0xffffffffu, !ok);
       tc_fence_after();
-      const float ev = e_s[row];
-      const bool act = act_s[row] != 0;
       // Read the per-column tables through volatile views: they are loop-invariant, and if
       // the compiler hoists them out of the iteration loop they cost ~190 registers.
       const volatile float* vb1t = b1t;
@@ -444,7 +442,7 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
       float dmax = 0.0f, smax = 0.0f;
       // tcgen05.ld / st are warp-collective: a warp with any active row runs them on every
       // lane; inactive lanes keep S_old (so they rewrite the same X) and report no change.
-      if (__any_sync(0xffffffffu, act)) {
+      if (!to && __any_sync(0xffffffffu, act)) {
 #pragma unroll
         for (int ch = 0; ch < C::NCH; ++ch) {
           const int c0 = cb + ch * C::CH;
@@ -486,56 +484,53 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
         }
         tmem_wait_st();
       }
-      red_d[half][row] = dmax;
-      red_s[half][row] = smax;
+      const int par = k & 1;
+      red_d[par][half][row] = dmax;
+      red_s[par][half][row] = smax;
       fence_async_smem();
       tc_fence_before();
-      __syncthreads();
-      // The next MMA only needs the X just written, so it is issued before the stop
-      // decision and overlaps the decision and the write-out.  If every row stops in this
-      // iteration, that MMA is not needed; it is waited for before the tile ends.
+      // The one barrier of the iteration: publishes X for the next MMA and the reduced
+      // changes, and tells every thread whether any row was active in this iteration.
+      const int any = __syncthreads_or(act ? 1 : 0);
+      if (abort_s) {
+        aborted = true;
+        break;
+      }
+      if (!any) break;  // the MMA waited for above was surplus; nothing is in flight
       if (tid == 0) {
         tc_fence_after();
         issue_mmas<NA>(tmem, aHi, aLo, bB);
         mma_commit(&mbar);
       }
-      // per-voxel stop decision (one thread per row)
-      int still = 0;
-      if (tid < kM) {
-        newly_s[tid] = 0;
-        if (act_s[tid]) {
-          float D = red_d[0][tid], Sm = red_s[0][tid];
+      // stop decision for this thread's row (identical in the row's column groups)
+      bool mine = false;
+      if (act) {
+        float D = red_d[par][0][row], Sm = red_s[par][0][row];
 #pragma unroll
-          for (int gi = 1; gi < kGroups; ++gi) {
-            D = fmaxf(D, red_d[gi][tid]);
-            Sm = fmaxf(Sm, red_s[gi][tid]);
-          }
-          const float r = rho_s[tid];
-          if (D < best_s[tid]) {
-            best_s[tid] = D;
-            stall_s[tid] = 0;
-          } else {
-            stall_s[tid] += 1;
-          }
-          const float scale = fmaxf(Sm, 1e-6f * s_glob);
-          // error bound within tol, or the change stopped shrinking (noise floor)
-          const bool conv = (r / (1.0f - r)) * D <= tol * scale || stall_s[tid] >= 3;
-          if (conv || k >= max_iters) {
-            act_s[tid] = 0;
-            newly_s[tid] = 1;
-            iters_s[tid] = k;
-            if (!conv) atomicAdd(rs.nonconv, 1);
-          } else {
-            still = 1;
-          }
+        for (int gi = 1; gi < kGroups; ++gi) {
+          D = fmaxf(D, red_d[par][gi][row]);
+          Sm = fmaxf(Sm, red_s[par][gi][row]);
+        }
+        if (D < best) {
+          best = D;
+          stall = 0;
+        } else {
+          stall += 1;
+        }
+        const float scale = fmaxf(Sm, 1e-6f * s_glob);
+        // error bound within tol, or the change stopped shrinking (noise floor)
+        const bool conv = (rho / (1.0f - rho)) * D <= tol * scale || stall >= 3;
+        if (conv || k >= max_iters) {
+          act = false;
+          mine = true;
+          iters = k;
+          if (!conv && half == 0) atomicAdd(rs.nonconv, 1);
         }
       }
-      n_active = __syncthreads_count(still);
       // write out the voxels that stopped in this iteration: I = Q + b1 S, S (Q from
       // registers: no global load on this path).  The addresses derive from a volatile
       // shared copy of the plane size so the compiler cannot hoist 2 x HALF 64-bit
       // addresses out of the iteration loop into registers.
-      const bool mine = newly_s[row] != 0;
       if (__any_sync(0xffffffffu, mine)) {  // warp-uniform: the TMEM loads are collective
         const size_t pl = static_cast<size_t>(*reinterpret_cast<volatile const int*>(&plane_s));
         float* pI = Iring + cur_base + static_cast<size_t>(cb) * pl + v;
@@ -562,22 +557,12 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
         }
         if (mine) esum += static_cast<double>(esum_row) * static_cast<double>(nidx[v]);
       }
-      if (n_active == 0) {
-        // drain the MMA issued above, so the barrier's phase and the tensor memory are
-        // free for the next tile
-        const bool ok2 = mbar_wait_bounded(&mbar, phase);
-        phase ^= 1u;
-        if (__syncthreads_or(!ok2)) aborted = true;
-        tc_fence_after();
-        break;
-      }
     }
     if (aborted) break;
-    // iteration statistics of this tile
+    // iteration statistics of this tile (group-0 threads hold one row each)
     if (warp < 4) {
-      int it = (v0 + tid < g.nv) ? iters_s[tid] : 0;
-      unsigned long long is = static_cast<unsigned long long>(it);
-      int im = it;
+      int im = vin ? iters : 0;
+      unsigned long long is = static_cast<unsigned long long>(vin ? iters : 0);
 #pragma unroll
       for (int o = 16; o >= 1; o >>= 1) {
         im = max(im, __shfl_xor_sync(0xffffffffu, im, o));
