@@ -17,7 +17,7 @@ bounded voxel sample), "e2e" (the whole job through the public API from host buf
 statistics of the window), "fp32" (the plain-FP32 path on the same window, when the
 headline precision is BF16).
 
---impl reference times the oracle alone (see cpu_leg) on the same workload.
+--impl reference times the oracle alone (see CpuLeg) on the same workload.
 """
 import argparse
 import json
@@ -85,31 +85,39 @@ def dist_env():
 
 # ------------------------------------------------------------------ CPU (oracle) leg
 
-def cpu_leg(prob, n_voxels, seed):
-    """Time the FP64 oracle's work for one time step at ``n_voxels`` random voxels (all
+class CpuLeg:
+    """The FP64 oracle's work for one time step at a random voxel sample (all
     directions): the upwind gather, Eq. 10 and the per-voxel source iteration, from a
     smooth synthetic developed history (the CPU cannot reach the developed part of the
-    solve itself: one full-grid oracle step takes about 30 s).  Returns (updates/s, info)."""
-    from oracle.solver import Model, one_step_at
-    model = Model(dict(prob, tol=prob.get("tol", 1e-6)))
-    Ih, Sh = W.developed_history(prob, seed=seed)
-    levels = Ih.shape[0]
+    solve itself: one full-grid oracle step takes about 30 s).  The oracle's model and the
+    history are built once; each sample is timed on its own."""
 
-    def hist(which, lev, d, u):
-        arr = Ih if which == "I" else Sh
-        out = np.zeros(np.shape(lev))
-        ok = (lev < 0) & (lev >= -levels)
-        out[ok] = arr[levels + lev[ok], d[ok], u[ok]]
-        return out
+    def __init__(self, prob, seed=7):
+        from oracle.solver import Model
+        self.model = Model(dict(prob, tol=prob.get("tol", 1e-6)))
+        self.Ih, self.Sh = W.developed_history(prob, seed=seed)
+        self.s_glob = float(np.abs(self.Sh[-1]).max())
 
-    rng = np.random.default_rng(seed)
-    vox = np.sort(rng.choice(model.nv, n_voxels, replace=False))
-    s_glob = float(np.abs(Sh[-1]).max())
-    t0 = time.perf_counter()
-    _, _, iters = one_step_at(model, 0, hist, vox, s_glob)
-    dt = time.perf_counter() - t0
-    return n_voxels * model.na / dt, dict(seconds=dt, voxels=int(n_voxels),
-                                          iters_mean=float(np.mean(iters)))
+    def sample(self, n_voxels, seed):
+        """(updates/s, info) of one step at ``n_voxels`` random voxels."""
+        from oracle.solver import one_step_at
+        Ih, Sh = self.Ih, self.Sh
+        levels = Ih.shape[0]
+
+        def hist(which, lev, d, u):
+            arr = Ih if which == "I" else Sh
+            out = np.zeros(np.shape(lev))
+            ok = (lev < 0) & (lev >= -levels)
+            out[ok] = arr[levels + lev[ok], d[ok], u[ok]]
+            return out
+
+        rng = np.random.default_rng(seed)
+        vox = np.sort(rng.choice(self.model.nv, n_voxels, replace=False))
+        t0 = time.perf_counter()
+        _, _, iters = one_step_at(self.model, 0, hist, vox, self.s_glob)
+        dt = time.perf_counter() - t0
+        return n_voxels * self.model.na / dt, dict(seconds=dt, voxels=int(n_voxels),
+                                                   iters_mean=float(np.mean(iters)))
 
 
 def cpu_cores():
@@ -127,8 +135,9 @@ def run_reference(args):
     prob = W.config_slab(steps=args.spinup + args.warmup + args.steps, nx=nx, ny=ny, nz=nz)
     vals = []
     info = None
+    leg = CpuLeg(prob)
     for k in range(args.warmup + args.steps):
-        v, info = cpu_leg(prob, args.ref_voxels, seed=100 + k)
+        v, info = leg.sample(args.ref_voxels, seed=100 + k)
         if k >= args.warmup:
             vals.append(v)
     value = float(np.mean(vals))
@@ -413,7 +422,7 @@ def main():
         f32.close()
 
     if rank == 0 and not args.no_cpu and ws >= 1:
-        v, info = cpu_leg(prob, args.cpu_voxels, seed=100)
+        v, info = CpuLeg(prob).sample(args.cpu_voxels, seed=100)
         line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": cpu_cores(),
                                 "kind": "oracle",
                                 "sample": "one time step of the FP64 oracle at %d random voxels x 192 "
