@@ -55,3 +55,61 @@ def ring_directions(nside):
 def pixel_weight(nside):
     """Solid angle of one pixel, 4 pi / N_a (equal-area pixels)."""
     return 4.0 * np.pi / (12 * nside * nside)
+
+
+def ring_pixel(nside, z, phi):
+    """RING index of the pixel containing each direction (z = cos theta, phi), FP64.
+
+    Restated from the pixel boundaries of the HEALPix construction (Gorski et al. 2005):
+      belt (|z| <= 2/3): with t = 2 nside phi / pi (one unit per pixel along a ring) and
+        w = 3 nside z / 2 (one unit per ring), pixels are the unit squares of the rotated
+        lattice a = t + w/2, b = t - w/2, whose centres sit at (N - 1)/2 + integers;
+        the centre (a0, b0) gives ring i = 2N - (a0 - b0) and j = (a0 + b0 + s)/2 with
+        s = (i - N + 1) mod 2 (j taken modulo 4N);
+      caps (|z| > 2/3): with sigma = N sqrt(3 (1 - |z|)) and tp the fraction of phi within
+        its quarter, pixel boundaries are the curves x = tp sigma = k and
+        y = (1 - tp) sigma = k, so ring i = floor(x) + floor(y) + 1 (counted from the
+        pole) and, in quarter q, j = q i + floor(x) + 1.
+    """
+    z = np.asarray(z, dtype=np.float64)
+    phi = np.mod(np.asarray(phi, dtype=np.float64), 2.0 * np.pi)
+    N = nside
+    npix = 12 * N * N
+    out = np.empty(z.shape, dtype=np.int64)
+    belt = np.abs(z) <= 2.0 / 3.0
+    # belt
+    t = 2.0 * N * phi[belt] / np.pi
+    w = 1.5 * N * z[belt]
+    off = (N - 1) / 2.0
+    a0 = np.floor(t + w / 2.0 - off + 0.5) + off
+    b0 = np.floor(t - w / 2.0 - off + 0.5) + off
+    i = np.rint(2 * N - (a0 - b0)).astype(np.int64)
+    s = (i - N + 1) % 2
+    j = np.rint((a0 + b0 + s) / 2.0).astype(np.int64)
+    j = (j - 1) % (4 * N) + 1
+    out[belt] = 2 * N * (N - 1) + 4 * N * (i - N) + (j - 1)
+    # caps
+    cap = ~belt
+    zc, pc = z[cap], phi[cap]
+    sigma = N * np.sqrt(3.0 * (1.0 - np.abs(zc)))
+    quarter = np.minimum(np.floor(pc / (np.pi / 2.0)), 3.0)
+    tp = pc / (np.pi / 2.0) - quarter
+    kx = np.floor(tp * sigma)
+    ky = np.floor((1.0 - tp) * sigma)
+    ic = (kx + ky + 1).astype(np.int64)
+    jc = (quarter * ic + kx + 1).astype(np.int64)
+    north = zc > 0
+    out_c = np.where(north, 2 * ic * (ic - 1) + (jc - 1), npix - 2 * ic * (ic + 1) + (jc - 1))
+    out[cap] = out_c
+    return out
+
+
+def parent_map(nside_fine, nside_coarse):
+    """Coarse pixel (RING) of every fine pixel: the coarse pixel that contains the fine
+    pixel's centre.  HEALPix pixels nest, so every coarse pixel is the union of its
+    (nside_fine / nside_coarse)^2 children (the paper's 16 finer angles per source-function
+    bin, §2.1, when 3072 transport directions feed 192 source-function directions)."""
+    if nside_fine % nside_coarse:
+        raise ValueError("nside_fine must be a multiple of nside_coarse")
+    z, phi = ring_z_phi(nside_fine)
+    return ring_pixel(nside_coarse, z, phi)

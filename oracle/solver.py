@@ -153,7 +153,10 @@ class Model:
         self.dirs = ring_directions(prob["nside"])
         self.na = self.dirs.shape[0]
         self.w = pixel_weight(prob["nside"])
-        self.P = phase_matrix(prob["nside"], float(prob["g"]))
+        # the source function's angular grid (§2.1: 192 bins fed by 3072 transport bins
+        # in the paper's fiducial runs); the transport grid unless a coarser one is named
+        self.nside_s = int(prob.get("nside_scatter") or prob["nside"])
+        self.P = phase_matrix(self.nside_s, float(prob["g"]))
         self.periodic = prob.get("boundary", "vacuum") == "periodic"
         self.lat = RayLattice(self.dirs, self.shape, self.h, self.periodic)
         self.dt = time_step(prob["courant"], self.h, prob["n_ref"])
