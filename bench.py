@@ -271,6 +271,135 @@ def run_serve(args):
     print(json.dumps(line))
 
 
+def run_adjoint(args):
+    """Gradient workload (--adjoint): 64^3 voxels, 192 directions, 800 steps, 8 detectors,
+    log-normal random-field optics; least-squares misfit between its detector curves and
+    those of a map with a 20 % mu_a blob; gradient with respect to mu_a and mu_s per voxel
+    by the checkpointed forward (every 50 steps) and the reverse sweep, FP32 with FP64
+    sums.  value = cell*dir*step updates per second of the whole gradient (forward +
+    reverse, device time); e2e = the same through the public API from host buffers; the
+    gradient is checked against a central difference, along a random smooth direction
+    through every voxel, of sum G E(mu) with the residual G frozen (two more forward
+    solves, untimed)."""
+    import torch
+    import paper_2105_01028_gb300 as T
+    torch.cuda.set_device(0)
+    n, steps, every = args.adjoint_grid, args.adjoint_steps, 50
+    p, q = W.config_adjoint(n=n, steps=steps)
+    nv, na = n ** 3, 12 * p["nside"] ** 2
+    stream = torch.cuda.Stream()
+    fq = T.Forward(q, stream=stream.cuda_stream)
+    fq.run(steps)
+    fq.sync()
+    obs = fq.detectors()
+    fq.close()
+    # first-use costs (library load, module load, allocator) on a small case
+    pw, _ = W.config_adjoint(n=16, steps=20)
+    fw = T.Forward(pw, stream=stream.cuda_stream)
+    fw.run_checkpointed(20, 10)
+    fw.adjoint(fw.detectors())
+    fw.close()
+    torch.cuda.synchronize()
+
+    t_job0 = time.perf_counter()
+    fw = T.Forward(p, stream=stream.cuda_stream)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    with ClockSampler(0) as clk:
+        e[0].record(stream)
+        fw.run_checkpointed(steps, every)
+        e[1].record(stream)
+        det = fw.detectors()
+        G = det - obs
+        e[2].record(stream)
+        ga, gs, st = fw.adjoint_profile(G)
+        e[3].record(stream)
+        stream.synchronize()
+    t_job = time.perf_counter() - t_job0
+    status = int(fw.last_status)
+    ms_fwd = e[0].elapsed_time(e[1])
+    ms_adj = e[2].elapsed_time(e[3])
+    fit, fit_mean = fw.iterations()
+    fw.close()
+    L = 0.5 * float(np.sum(G * G))
+
+    # directional central difference through every voxel (untimed), of sum G E(mu) with
+    # the residual G frozen: the same gradient J^T G without the misfit's curvature
+    rng = np.random.default_rng(8)
+    da = W.gaussian_random_field(p["mua"].shape, 3.0, 1.0, rng).astype(np.float32)
+    ds = W.gaussian_random_field(p["mus"].shape, 3.0, 1.0, rng).astype(np.float32)
+    t = 3e-3
+    Ls = []
+    for sgn in (1.0, -1.0):
+        pp = dict(p, mua=(p["mua"] * (1 + sgn * t * da)).astype(np.float32),
+                  mus=(p["mus"] * (1 + sgn * t * ds)).astype(np.float32))
+        f = T.Forward(pp, stream=stream.cuda_stream)
+        f.run(steps)
+        f.sync()
+        Ls.append(float(np.sum(G * f.detectors())))
+        f.close()
+    fd = (Ls[0] - Ls[1]) / (2 * t)
+    ad = float(np.sum(ga * (p["mua"] * da).ravel()) + np.sum(gs * (p["mus"] * ds).ravel()))
+
+    pk = peaks()
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    hbm = pk["hbm_gbs"]
+    upd = nv * na * steps
+    it_adj = float(st[6])
+    solve_flops = 2.0 * na * na * nv * it_adj * steps
+    solve_ach = solve_flops / (st[3] * 1e-3) / 1e12
+    push_bytes = nv * na * 52.0 * steps  # Qpre 4, I/S at two levels 16, Ibar/Sbar RMW 32
+    push_ach = push_bytes / (st[4] * 1e-3) / 1e9
+    copy_bytes = nv * na * 16.0 * steps  # I and S of every level read and written once
+    copy_ach = copy_bytes / (st[2] * 1e-3) / 1e9
+    fwd_flops = 2.0 * na * na * nv * float(np.mean(fit_mean)) * steps
+    phases = [
+        {"name": "forward, checkpointed (sweep + scatter_fp32 + tallies)", "ms": ms_fwd},
+        {"name": "checkpoint restores", "ms": st[0]},
+        {"name": "recomputed forward steps", "ms": st[1]},
+        {"name": "segment-store copies", "ms": st[2], "bound": "hbm", "achieved": copy_ach, "peak": hbm,
+         "unit": "GB/s", "frac": copy_ach / hbm},
+        {"name": "adj_scatter_fp32 (transposed solve) + injection", "ms": st[3], "bound": "alu",
+         "achieved": solve_ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": solve_ach / fp32_peak,
+         "iterations_mean": it_adj},
+        {"name": "adj_push (+ transposed interface split)", "ms": st[4], "bound": "hbm",
+         "achieved": push_ach, "peak": hbm, "unit": "GB/s", "frac": push_ach / hbm,
+         "algorithmic_bytes_per_update": 52},
+        {"name": "gradient finish", "ms": st[5]},
+    ]
+    tot = ms_fwd + ms_adj
+    for ph in phases:
+        ph["share"] = ph["ms"] / tot
+    line = {"metric": "adjoint gradient cell*dir*step updates/s", "value": upd / (tot * 1e-3),
+            "unit": "updates/s", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": tot,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "gradient: %d^3 voxels @1mm, 192 HEALPix dirs, %d time steps, 8 "
+                                   "detectors, log-normal GRF optics (mu_a 0.01, mu_s 10 /mm), misfit "
+                                   "against a 20%% mu_a blob, checkpoints every %d steps" % (n, steps, every),
+                       "step": "one bench step = one whole gradient (forward with checkpoints + reverse sweep)",
+                       "l2": "inputs larger than L2 (%.1f GB of checkpoints and segment store)"
+                             % (T.adjoint_footprint_bytes(p, steps, every) / 1e9)},
+            "gpu_launches": int(8 * steps + 3 * steps + (steps + every - 1) // every + 2),
+            "status": status,
+            "roofline": {"kernel": "adj_scatter_fp32", "bound": "alu", "achieved": solve_ach,
+                         "peak": fp32_peak, "unit": "TFLOP/s", "frac": solve_ach / fp32_peak,
+                         "traffic": measured_traffic("adj_scatter_fp32_kernel", nv * na),
+                         "peak_source": "FP32 FFMA: 152 SMs x 128 lanes x 2 x max SM clock"},
+            "phases": phases,
+            "forward_scatter_tflops": fwd_flops / (ms_fwd * 1e-3) / 1e12,
+            "misfit": L, "grad_max": {"mua": float(np.abs(ga).max()), "mus": float(np.abs(gs).max())},
+            "fd_check": {"direction": "smooth random field (std 3 mm) on both maps, 0.3 % amplitude; "
+                                      "differences of sum G E(mu) with the residual G frozen",
+                         "central_difference": fd, "adjoint": ad, "rel_err": abs(fd - ad) / abs(ad)},
+            "clocks": clk.summary(),
+            "e2e": {"value": upd / t_job, "unit": "updates/s",
+                    "what": "whole gradient from host buffers: context + optics upload, checkpointed "
+                            "forward, curves read back, dL/dE up, reverse sweep, gradients read back",
+                    "h2d_bytes_per_step": 3 * nv * 4 + G.size * 8,
+                    "d2h_bytes_per_step": det.size * 8 + 2 * nv * 8}}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -292,6 +421,9 @@ def main():
                     help="run the served stream with N requests instead of the slab")
     ap.add_argument("--rate", type=float, default=8.0, help="served stream arrival rate (1/s)")
     ap.add_argument("--slots", type=int, default=8, help="served stream concurrent slots")
+    ap.add_argument("--adjoint", action="store_true", help="gradient workload (checkpointed adjoint)")
+    ap.add_argument("--adjoint-grid", type=int, default=64)
+    ap.add_argument("--adjoint-steps", type=int, default=800)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -300,6 +432,9 @@ def main():
         return
     if args.serve:
         run_serve(args)
+        return
+    if args.adjoint:
+        run_adjoint(args)
         return
 
     import torch

@@ -187,6 +187,51 @@ void trinity_destroy(trinity_ctx* ctx);
  * layouts, descriptors and TMEM read-out as the iteration kernel.  For testing. */
 int trinity_tc_selftest(int na, const uint16_t* A, const uint16_t* B, float* D);
 
+/* ---- Adjoint: gradient of a detector misfit with respect to mu_a and mu_s. ----
+ *
+ * The paper has no adjoint (Section 4 names inverse problems as future work).  These
+ * calls give the exact reverse-mode derivative of the discrete forward model above
+ * (Eqs. 9, 10, 12 and the index interfaces of Eqs. 13-14) for a scalar misfit L whose
+ * derivative with respect to the detector curves, dL/dE [n_det][nbins], the caller
+ * supplies.  The reverse sweep gathers nothing: each voxel pushes its ray adjoint to its
+ * upwind sample at the two retarded levels it was interpolated from, and the transposed
+ * scattering solve y = a P (q + b1 y) is the forward iteration again (P is symmetric).
+ * Forward levels are recomputed from checkpoints segment by segment.  All reverse-sweep
+ * arithmetic is FP32 with FP64 gradient sums; in TRINITY_BF16 mode the recomputed
+ * forward steps run in BF16 (as the original ones did) and the reverse sweep in FP32. */
+
+/* Device bytes that trinity_run_checkpointed plus trinity_adjoint add to a context:
+ * ceil(nsteps / every) + 1 checkpoints of 4 levels of I and S, a store of every + 4
+ * levels of I and S for one segment, the adjoint levels and the gradient sums.  0 for
+ * invalid arguments. */
+size_t trinity_adjoint_footprint_bytes(const trinity_grid_desc* desc, int nsteps, int every, int n_det,
+                                       int nbins);
+
+/* Run ``nsteps`` forward steps from step 0 (the context must be fresh or reset), saving
+ * the state before steps 0, every, 2 every, ... and after the last step (levels n-4..n-1
+ * of I and S and max |S(n-1)|: everything a step reads).  Same results as trinity_step.
+ * TRINITY_E_OOM if the checkpoints do not fit; TRINITY_E_STATE if steps were taken. */
+int trinity_run_checkpointed(trinity_ctx* ctx, int nsteps, int every);
+
+/* Reverse sweep over the steps of the last trinity_run_checkpointed (no steps may follow
+ * it).  dL_dE: FP64 [n_det][nbins], n = n_det * nbins.  grad_mua, grad_mus: FP64
+ * [nz*ny*nx], receive dL/dmu_a and dL/dmu_s per voxel (where mu_a = mu_s = 0 only the
+ * transport term, the albedo there being undefined).  ptr_kind applies to all three
+ * pointers.  The forward state after the last step is restored, so stepping may continue
+ * (after which the checkpoints no longer apply).  May be called again with another dL_dE.
+ * Returns TRINITY_W_NOT_CONVERGED if a transposed solve hit max_iters somewhere. */
+int trinity_adjoint(trinity_ctx* ctx, const double* dL_dE, size_t n, double* grad_mua, double* grad_mus,
+                    int ptr_kind);
+
+/* trinity_adjoint with CUDA events around each phase (on the context's stream).  stats
+ * (host, 7 doubles) receives the summed device ms of [0] checkpoint restores, [1] the
+ * recomputed forward steps, [2] the copies into the segment store, [3] detector injection
+ * and transposed scattering solves, [4] transposed interface splits and upwind pushes,
+ * [5] the final gradient kernel, and [6] the mean iterations of the transposed solves
+ * per voxel and step.  For measurement. */
+int trinity_adjoint_profile(trinity_ctx* ctx, const double* dL_dE, size_t n, double* grad_mua,
+                            double* grad_mus, int ptr_kind, double* stats);
+
 /* ---- Serving: many forward solves at once on one GPU. ----
  *
  * Reconstruction needs many forward models.  A server queues solve requests and admits

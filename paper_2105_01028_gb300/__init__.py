@@ -17,7 +17,8 @@ FIELD_I, FIELD_S = 0, 1
 _PREC = {"fp32": FP32, "bf16": BF16}
 _BOUND = {"vacuum": 0, "periodic": 1}
 
-__all__ = ["Forward", "Server", "TrinityError", "grid_desc", "footprint_bytes", "healpix_dirs",
+__all__ = ["Forward", "Server", "TrinityError", "grid_desc", "footprint_bytes",
+           "adjoint_footprint_bytes", "healpix_dirs",
            "phase_matrix", "lattice_tables", "cone_weights", "lib"]
 
 
@@ -36,6 +37,14 @@ def grid_desc(prob):
 def footprint_bytes(prob):
     d = grid_desc(prob)
     return int(lib().trinity_footprint_bytes(ctypes.byref(d)))
+
+
+def adjoint_footprint_bytes(prob, nsteps, every=50):
+    """Extra device bytes of a checkpointed run plus its adjoint."""
+    d = grid_desc(prob)
+    return int(lib().trinity_adjoint_footprint_bytes(ctypes.byref(d), int(nsteps), int(every),
+                                                     len(prob.get("detectors", [])),
+                                                     int(prob.get("nbins", 1))))
 
 
 def _ptr(a):
@@ -143,6 +152,57 @@ class Forward:
     def sync(self):
         self.last_status = self._check(self.L.trinity_sync(self.h))
         return self.last_status
+
+    # -- adjoint
+    def run_checkpointed(self, nsteps, every=50):
+        """``nsteps`` steps from step 0, saving checkpoints every ``every`` steps for
+        ``adjoint`` (synchronous)."""
+        self.last_status = self._check(self.L.trinity_run_checkpointed(self.h, int(nsteps), int(every)))
+        return self.last_status
+
+    def adjoint(self, dL_dE, out=None):
+        """dL/dmu_a, dL/dmu_s per voxel (FP64, flat [N_v]) for the misfit whose gradient
+        with respect to the detector curves is ``dL_dE`` [n_det, nbins].  With ``out`` =
+        (ga, gs), two contiguous float64 CUDA tensors of N_v elements, the gradients are
+        written there and dL_dE may be a CUDA tensor too."""
+        if out is not None:
+            ga, gs = out
+            if not (getattr(ga, "is_cuda", False) and getattr(gs, "is_cuda", False)
+                    and getattr(dL_dE, "is_cuda", False)):
+                raise ValueError("device outputs need a device dL_dE")
+            for t in (dL_dE, ga, gs):
+                if not t.is_contiguous() or str(t.dtype) != "torch.float64":
+                    raise ValueError("device adjoint buffers must be contiguous float64")
+            self.last_status = self._check(self.L.trinity_adjoint(
+                self.h, ctypes.c_void_p(dL_dE.data_ptr()), dL_dE.numel(),
+                ctypes.c_void_p(ga.data_ptr()), ctypes.c_void_p(gs.data_ptr()), 1))
+            return ga, gs
+        G = self._grad_input(dL_dE)
+        ga = np.zeros(self.nv)
+        gs = np.zeros(self.nv)
+        self.last_status = self._check(self.L.trinity_adjoint(
+            self.h, G.ctypes.data_as(ctypes.c_void_p), G.size, ga.ctypes.data_as(ctypes.c_void_p),
+            gs.ctypes.data_as(ctypes.c_void_p), 0))
+        return ga, gs
+
+    def adjoint_profile(self, dL_dE):
+        """``adjoint`` with per-phase device times: returns (ga, gs, stats), stats as in
+        trinity_adjoint_profile (ms of restores, recomputed steps, store copies, transposed
+        solves, pushes, final kernel; mean transposed-solve iterations)."""
+        G = self._grad_input(dL_dE)
+        ga = np.zeros(self.nv)
+        gs = np.zeros(self.nv)
+        st = np.zeros(7)
+        self.last_status = self._check(self.L.trinity_adjoint_profile(
+            self.h, G.ctypes.data_as(ctypes.c_void_p), G.size, ga.ctypes.data_as(ctypes.c_void_p),
+            gs.ctypes.data_as(ctypes.c_void_p), 0, st.ctypes.data_as(_lib.P_double)))
+        return ga, gs, st
+
+    def _grad_input(self, dL_dE):
+        G = np.ascontiguousarray(dL_dE, dtype=np.float64)
+        if G.size != self.n_det * self.nbins:
+            raise ValueError("dL_dE must have n_det * nbins entries")
+        return G
 
     def reset(self):
         return self._check(self.L.trinity_reset(self.h))

@@ -71,6 +71,10 @@ SIGNATURES = {
     "trinity_last_error": (ctypes.c_char_p, [c_void_p]),
     "trinity_destroy": (None, [c_void_p]),
     "trinity_tc_selftest": (c_int, [c_int, c_void_p, c_void_p, c_void_p]),
+    "trinity_adjoint_footprint_bytes": (c_size_t, [ctypes.POINTER(GridDesc), c_int, c_int, c_int, c_int]),
+    "trinity_run_checkpointed": (c_int, [c_void_p, c_int, c_int]),
+    "trinity_adjoint": (c_int, [c_void_p, c_void_p, c_size_t, c_void_p, c_void_p, c_int]),
+    "trinity_adjoint_profile": (c_int, [c_void_p, c_void_p, c_size_t, c_void_p, c_void_p, c_int, P_double]),
     "trinity_source_iteration_noalloc": (c_int, [c_int, c_int] + [c_void_p] * 7 +
                                          [c_double, c_int, P_int, c_void_p]),
     "trinity_serve_create": (c_int, [c_size_t, c_int, c_int, ctypes.POINTER(c_void_p)]),

@@ -83,6 +83,28 @@ struct trinity_ctx {
   int *d_if_vox = nullptr, *d_if_rowptr = nullptr, *d_if_src = nullptr;
   float* d_if_w = nullptr;
   uint8_t* d_if_keep = nullptr;
+  // the transposed split F^T in the same gather form (rows indexed by the crossing direction)
+  int *d_ift_rowptr = nullptr, *d_ift_src = nullptr;
+  float* d_ift_w = nullptr;
+
+  // adjoint: checkpoints of a checkpointed run and the reverse-sweep buffers
+  int ck_every = 0, ck_steps = 0, n_ckpt = 0;  // checkpoints at 0, every, ..., and at ck_steps
+  bool ck_valid = false;
+  float* d_ckpt = nullptr;          // [n_ckpt][I levels c-4..c-1, S levels c-4..c-1][na][nv]
+  unsigned* d_ckpt_smax = nullptr;  // [n_ckpt] max |S(c-1)|
+  float *d_stI = nullptr, *d_stS = nullptr;  // segment store [every + 4][na][nv]
+  float *d_aI = nullptr, *d_aS = nullptr;    // adjoint levels Ibar, Sbar [5][na][nv]
+  float *d_Qb = nullptr, *d_Y = nullptr;     // Qbar and the warm start of the transposed solve
+  double *d_gA = nullptr, *d_gmut = nullptr, *d_gmua = nullptr, *d_gmus = nullptr, *d_G = nullptr;
+  unsigned* d_ymax = nullptr;       // [2] max |y| of the last two reverse steps
+  int* d_adj_nonconv = nullptr;
+  unsigned long long* d_adj_iters = nullptr;  // iterations of the transposed solves, summed
+  // tallies of the recomputed forward steps go here, not into the run's own
+  int* d_re_iters_max = nullptr;
+  unsigned long long* d_re_iters_sum = nullptr;
+  double *d_re_energy = nullptr, *d_re_escaped = nullptr, *d_re_det = nullptr;
+  int* d_re_nonconv = nullptr;
+  int re_capacity = 0;
 };
 
 namespace {
@@ -274,8 +296,13 @@ void free_interfaces(trinity_ctx* c) {
   cudaFree(c->d_if_src);
   cudaFree(c->d_if_w);
   cudaFree(c->d_if_keep);
+  cudaFree(c->d_ift_rowptr);
+  cudaFree(c->d_ift_src);
+  cudaFree(c->d_ift_w);
   c->d_if_vox = c->d_if_rowptr = c->d_if_src = nullptr;
+  c->d_ift_rowptr = c->d_ift_src = nullptr;
   c->d_if_w = nullptr;
+  c->d_ift_w = nullptr;
   c->d_if_keep = nullptr;
   c->n_iface = 0;
 }
@@ -305,12 +332,106 @@ int build_interface_table(trinity_ctx* ctx) {
     CK(cudaMemcpy(ctx->d_if_w, T.w.data(), T.w.size() * sizeof(float), cudaMemcpyHostToDevice));
   }
   CK(cudaMemcpy(ctx->d_if_keep, T.keep.data(), T.keep.size(), cudaMemcpyHostToDevice));
+  // F^T: out[j] = keep[j] q[j] + sum over the entries (j -> d, w) of w q[d]
+  const int na = ctx->g.na;
+  std::vector<int> trp, tsrc;
+  std::vector<float> tw;
+  for (size_t i = 0; i < T.vox.size(); ++i) {
+    std::vector<std::vector<std::pair<int, float>>> rows(na);
+    for (int d = 0; d < na; ++d)
+      for (int e = T.rowptr[i * (na + 1) + d]; e < T.rowptr[i * (na + 1) + d + 1]; ++e)
+        rows[T.src[e]].push_back({d, T.w[e]});
+    for (int j = 0; j < na; ++j) {
+      trp.push_back(static_cast<int>(tsrc.size()));
+      for (const auto& e : rows[j]) {
+        tsrc.push_back(e.first);
+        tw.push_back(e.second);
+      }
+    }
+    trp.push_back(static_cast<int>(tsrc.size()));
+  }
+  CK(dalloc(&ctx->d_ift_rowptr, trp.size()));
+  CK(dalloc(&ctx->d_ift_src, tsrc.size()));
+  CK(dalloc(&ctx->d_ift_w, tw.size()));
+  CK(cudaMemcpy(ctx->d_ift_rowptr, trp.data(), trp.size() * sizeof(int), cudaMemcpyHostToDevice));
+  if (!tsrc.empty()) {
+    CK(cudaMemcpy(ctx->d_ift_src, tsrc.data(), tsrc.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_ift_w, tw.data(), tw.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  return TRINITY_OK;
+}
+
+void free_adjoint(trinity_ctx* c) {
+  void* bufs[] = {c->d_ckpt,      c->d_ckpt_smax,   c->d_stI,         c->d_stS,
+                  c->d_aI,        c->d_aS,          c->d_Qb,          c->d_Y,
+                  c->d_gA,        c->d_gmut,        c->d_gmua,        c->d_gmus,
+                  c->d_G,         c->d_ymax,        c->d_adj_nonconv, c->d_re_iters_max,
+                  c->d_re_iters_sum, c->d_re_energy, c->d_re_escaped, c->d_re_det,
+                  c->d_re_nonconv, c->d_adj_iters};
+  for (void* p : bufs)
+    if (p) cudaFree(p);
+  c->d_ckpt = c->d_stI = c->d_stS = c->d_aI = c->d_aS = c->d_Qb = c->d_Y = nullptr;
+  c->d_ckpt_smax = c->d_ymax = nullptr;
+  c->d_gA = c->d_gmut = c->d_gmua = c->d_gmus = c->d_G = nullptr;
+  c->d_re_energy = c->d_re_escaped = c->d_re_det = nullptr;
+  c->d_adj_nonconv = c->d_re_iters_max = c->d_re_nonconv = nullptr;
+  c->d_re_iters_sum = c->d_adj_iters = nullptr;
+  c->re_capacity = 0;
+  c->ck_valid = false;
+  c->n_ckpt = c->ck_every = c->ck_steps = 0;
+}
+
+size_t adjoint_bytes(size_t na, size_t nv, int nsteps, int every, int ndet_bins) {
+  const size_t lvl = na * nv * sizeof(float);
+  const size_t nck = static_cast<size_t>((nsteps + every - 1) / every) + 1;
+  size_t b = nck * 8 * lvl + nck * sizeof(unsigned);  // checkpoints
+  b += static_cast<size_t>(every + 4) * 2 * lvl;      // segment store
+  b += 12 * lvl;                                      // adjoint levels, Qbar, warm start
+  b += 4 * nv * sizeof(double);                       // gradient sums and outputs
+  b += static_cast<size_t>(ndet_bins) * 2 * sizeof(double) +
+       static_cast<size_t>(nsteps) * (2 * sizeof(double) + sizeof(int) + sizeof(unsigned long long));
+  return b;
+}
+
+// Copy levels c-4..c-1 of I and S (ring slots) into checkpoint k, with max |S(c-1)|.
+int save_checkpoint(trinity_ctx* ctx, int k, int c) {
+  const size_t lvl = static_cast<size_t>(ctx->g.na) * ctx->g.nv;
+  float* base = ctx->d_ckpt + static_cast<size_t>(k) * 8 * lvl;
+  for (int j = 0; j < 4; ++j) {
+    const size_t slot = static_cast<size_t>(ring_slot(c - 4 + j));
+    CK(cudaMemcpyAsync(base + j * lvl, ctx->I + slot * lvl, lvl * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(base + (4 + j) * lvl, ctx->S + slot * lvl, lvl * 4, cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+  }
+  CK(cudaMemcpyAsync(ctx->d_ckpt_smax + k, ctx->d_smax + ((c - 1) & 1), sizeof(unsigned),
+                     cudaMemcpyDeviceToDevice, ctx->stream));
+  return TRINITY_OK;
+}
+
+// Put checkpoint k (taken before step c) back into the ring, the step counter and smax;
+// with ``store`` also into the first four levels of the segment store.
+int restore_checkpoint(trinity_ctx* ctx, int k, int c, bool store) {
+  const size_t lvl = static_cast<size_t>(ctx->g.na) * ctx->g.nv;
+  const float* base = ctx->d_ckpt + static_cast<size_t>(k) * 8 * lvl;
+  for (int j = 0; j < 4; ++j) {
+    const size_t slot = static_cast<size_t>(ring_slot(c - 4 + j));
+    CK(cudaMemcpyAsync(ctx->I + slot * lvl, base + j * lvl, lvl * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->S + slot * lvl, base + (4 + j) * lvl, lvl * 4, cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+    if (store) {
+      CK(cudaMemcpyAsync(ctx->d_stI + j * lvl, base + j * lvl, lvl * 4, cudaMemcpyDeviceToDevice,
+                         ctx->stream));
+      CK(cudaMemcpyAsync(ctx->d_stS + j * lvl, base + (4 + j) * lvl, lvl * 4, cudaMemcpyDeviceToDevice,
+                         ctx->stream));
+    }
+  }
+  CK(launch_adj_restore(ctx->d_step, c, ctx->d_smax, ctx->d_ckpt_smax + k, ctx->stream));
   return TRINITY_OK;
 }
 
 // The launches of one time step (all on ctx->stream; the step index lives on the device).
-int enqueue_step(trinity_ctx* ctx) {
-  const RunState rs = run_state(ctx);
+// ``rs`` and ``det`` take the step's tallies.
+int enqueue_step_with(trinity_ctx* ctx, const RunState& rs, double* det) {
   const GridParams& g = ctx->g;
   CK(launch_sweep(g, ctx->d_dirs, ctx->d_offs, ctx->I, ctx->S, ctx->mut, ctx->nidx, ctx->Q, rs,
                   ctx->stream));
@@ -326,10 +447,12 @@ int enqueue_step(trinity_ctx* ctx) {
                            ctx->stream));
   }
   CK(launch_tally(g, ctx->d_dirs, ctx->I, ctx->d_det_vox, ctx->d_det_dir, ctx->d_det_w,
-                  ctx->d_det_id, ctx->n_det_entries, ctx->d_det, ctx->nbins, rs, ctx->stream));
+                  ctx->d_det_id, ctx->n_det_entries, det, ctx->nbins, rs, ctx->stream));
   CK(launch_advance(rs, ctx->stream));
   return TRINITY_OK;
 }
+
+int enqueue_step(trinity_ctx* ctx) { return enqueue_step_with(ctx, run_state(ctx), ctx->d_det); }
 
 int check_device_error(trinity_ctx* ctx) {
   int e = 0;
@@ -818,6 +941,232 @@ int trinity_profile_steps(trinity_ctx* ctx, int nsteps, double* kernel_ms) {
   return check_device_error(ctx);
 }
 
+size_t trinity_adjoint_footprint_bytes(const trinity_grid_desc* desc, int nsteps, int every, int n_det,
+                                       int nbins) {
+  std::string why;
+  if (!desc_valid(desc, &why) || nsteps < 1 || every < 1 || n_det < 0 || nbins < 1) return 0;
+  const size_t nv = static_cast<size_t>(desc->nx) * desc->ny * desc->nz;
+  const size_t na = 12u * desc->nside * desc->nside;
+  return adjoint_bytes(na, nv, nsteps, std::min(every, nsteps), n_det * nbins);
+}
+
+int trinity_run_checkpointed(trinity_ctx* ctx, int nsteps, int every) {
+  if (!ctx) return TRINITY_E_INVALID;
+  if (nsteps < 1 || every < 1) return fail(ctx, TRINITY_E_INVALID, "nsteps and every must be >= 1");
+  if (ctx->steps_done != 0)
+    return fail(ctx, TRINITY_E_STATE, "a checkpointed run starts at step 0 (call trinity_reset)");
+  int rc = lock_inputs(ctx);
+  if (rc != TRINITY_OK) return rc;
+  rc = ensure_capacity(ctx, nsteps);
+  if (rc != TRINITY_OK) return rc;
+  free_adjoint(ctx);
+  every = std::min(every, nsteps);
+  const size_t lvl = static_cast<size_t>(ctx->g.na) * ctx->g.nv;
+  const int nseg = (nsteps + every - 1) / every;
+  ctx->n_ckpt = nseg + 1;  // one before each segment and one after the last step
+  if (dalloc(&ctx->d_ckpt, static_cast<size_t>(ctx->n_ckpt) * 8 * lvl) != cudaSuccess ||
+      dalloc(&ctx->d_ckpt_smax, ctx->n_ckpt) != cudaSuccess) {
+    cudaGetLastError();
+    free_adjoint(ctx);
+    return fail(ctx, TRINITY_E_OOM, "no device memory for the checkpoints");
+  }
+  for (int k = 0; k < nseg; ++k) {
+    const int c = k * every;
+    rc = save_checkpoint(ctx, k, c);
+    if (rc != TRINITY_OK) return rc;
+    const int K = std::min(every, nsteps - c);
+    for (int s = 0; s < K; ++s) {
+      rc = enqueue_step(ctx);
+      if (rc != TRINITY_OK) return rc;
+    }
+  }
+  rc = save_checkpoint(ctx, nseg, nsteps);
+  if (rc != TRINITY_OK) return rc;
+  ctx->steps_done = nsteps;
+  ctx->ck_every = every;
+  ctx->ck_steps = nsteps;
+  ctx->ck_valid = true;
+  return trinity_sync(ctx);
+}
+
+namespace {
+
+// The reverse sweep.  With ``stats`` (7 doubles) each phase is bracketed by CUDA events
+// on the context's stream and the summed device ms are returned: [0] checkpoint restores,
+// [1] recomputed forward steps, [2] copies into the segment store, [3] detector injection
+// and transposed solves, [4] transposed interface splits and upwind pushes, [5] the
+// final gradient kernel; [6] = mean iterations of the transposed solves per voxel-step.
+int adjoint_impl(trinity_ctx* ctx, const double* dL_dE, size_t n, double* grad_mua, double* grad_mus,
+                 int ptr_kind, double* stats) {
+  if (!ctx) return TRINITY_E_INVALID;
+  if (!ctx->ck_valid || ctx->steps_done != ctx->ck_steps)
+    return fail(ctx, TRINITY_E_STATE, "trinity_adjoint needs a completed trinity_run_checkpointed "
+                                      "with no steps after it");
+  const int ndb = static_cast<int>(ctx->dets.size()) * ctx->nbins;
+  if (n != static_cast<size_t>(ndb) || (ndb > 0 && !dL_dE) || !grad_mua || !grad_mus ||
+      (ptr_kind != 0 && ptr_kind != 1))
+    return fail(ctx, TRINITY_E_INVALID, "bad adjoint arguments");
+  const GridParams& g = ctx->g;
+  const size_t nv = g.nv, lvl = static_cast<size_t>(g.na) * g.nv;
+  const int N = ctx->ck_steps, every = ctx->ck_every;
+  if (!ctx->d_stI) {
+    bool ok = dalloc(&ctx->d_stI, static_cast<size_t>(every + 4) * lvl) == cudaSuccess &&
+              dalloc(&ctx->d_stS, static_cast<size_t>(every + 4) * lvl) == cudaSuccess &&
+              dalloc(&ctx->d_aI, kRing * lvl) == cudaSuccess && dalloc(&ctx->d_aS, kRing * lvl) == cudaSuccess &&
+              dalloc(&ctx->d_Qb, lvl) == cudaSuccess && dalloc(&ctx->d_Y, lvl) == cudaSuccess &&
+              dalloc(&ctx->d_gA, nv) == cudaSuccess && dalloc(&ctx->d_gmut, nv) == cudaSuccess &&
+              dalloc(&ctx->d_gmua, nv) == cudaSuccess && dalloc(&ctx->d_gmus, nv) == cudaSuccess &&
+              dalloc(&ctx->d_G, ndb) == cudaSuccess && dalloc(&ctx->d_ymax, 2) == cudaSuccess &&
+              dalloc(&ctx->d_adj_nonconv, 1) == cudaSuccess && dalloc(&ctx->d_adj_iters, 1) == cudaSuccess &&
+              dalloc(&ctx->d_re_iters_max, N) == cudaSuccess &&
+              dalloc(&ctx->d_re_iters_sum, N) == cudaSuccess &&
+              dalloc(&ctx->d_re_energy, N) == cudaSuccess && dalloc(&ctx->d_re_escaped, N) == cudaSuccess &&
+              dalloc(&ctx->d_re_det, ndb) == cudaSuccess && dalloc(&ctx->d_re_nonconv, 1) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      return fail(ctx, TRINITY_E_OOM, "no device memory for the adjoint buffers");
+    }
+    ctx->re_capacity = N;
+  }
+  if (ndb > 0)
+    CK(cudaMemcpyAsync(ctx->d_G, dL_dE, ndb * sizeof(double),
+                       ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_aI, 0, kRing * lvl * 4, ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_aS, 0, kRing * lvl * 4, ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_Y, 0, lvl * 4, ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_gA, 0, nv * 8, ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_gmut, 0, nv * 8, ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_ymax, 0, 2 * sizeof(unsigned), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_adj_nonconv, 0, sizeof(int), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_adj_iters, 0, sizeof(unsigned long long), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_re_det, 0, std::max(ndb, 1) * sizeof(double), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_re_iters_max, 0, N * sizeof(int), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_re_iters_sum, 0, N * sizeof(unsigned long long), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_re_energy, 0, N * sizeof(double), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_re_escaped, 0, N * sizeof(double), ctx->stream));
+  RunState rs = run_state(ctx);  // recomputed steps: same step counter, smax and bins
+  rs.iters_max = ctx->d_re_iters_max;
+  rs.iters_sum = ctx->d_re_iters_sum;
+  rs.energy = ctx->d_re_energy;
+  rs.escaped = ctx->d_re_escaped;
+  rs.nonconv = ctx->d_re_nonconv;
+  const double bw = ctx->bin_ps * 1e-3;
+  const float tol = static_cast<float>(ctx->desc.tol);
+  const int nseg = ctx->n_ckpt - 1;
+  // phase timing: one event before and one after each phase instance
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs[6];
+  auto mark = [&](int phase, bool start) -> cudaError_t {
+    if (!stats) return cudaSuccess;
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    if (start)
+      evs[phase].push_back({e, nullptr});
+    else
+      evs[phase].back().second = e;
+    return cudaEventRecord(e, ctx->stream);
+  };
+  for (int k = nseg - 1; k >= 0; --k) {
+    const int c = k * every;
+    const int K = std::min(every, N - c);
+    const int lev_base = c - 4;
+    CK(mark(0, true));
+    int rc = restore_checkpoint(ctx, k, c, true);
+    if (rc != TRINITY_OK) return rc;
+    CK(mark(0, false));
+    for (int s = 0; s < K; ++s) {  // recompute the segment, keeping every level
+      CK(mark(1, true));
+      rc = enqueue_step_with(ctx, rs, ctx->d_re_det);
+      if (rc != TRINITY_OK) return rc;
+      CK(mark(1, false));
+      const int lev = c + s;
+      const size_t slot = static_cast<size_t>(ring_slot(lev));
+      const size_t dst = static_cast<size_t>(lev - lev_base) * lvl;
+      CK(mark(2, true));
+      CK(cudaMemcpyAsync(ctx->d_stI + dst, ctx->I + slot * lvl, lvl * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+      CK(cudaMemcpyAsync(ctx->d_stS + dst, ctx->S + slot * lvl, lvl * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+      CK(mark(2, false));
+    }
+    for (int lev = c + K - 1; lev >= c; --lev) {
+      const long b = floor_snap((lev + 0.5) * ctx->dt / bw);
+      const int bin = (b >= 0 && b < ctx->nbins) ? static_cast<int>(b) : -1;
+      float* aI_n = ctx->d_aI + static_cast<size_t>(ring_slot(lev)) * lvl;
+      float* aS_n = ctx->d_aS + static_cast<size_t>(ring_slot(lev)) * lvl;
+      const size_t here = static_cast<size_t>(lev - lev_base) * lvl;
+      CK(mark(3, true));
+      CK(launch_adj_inject(ctx->d_det_vox, ctx->d_det_dir, ctx->d_det_w, ctx->d_det_id, ctx->n_det_entries,
+                           ctx->d_G, ctx->nbins, bin, aI_n, g.nv, ctx->d_ymax + (lev & 1), ctx->stream));
+      CK(launch_adj_scatter_fp32(g, ctx->d_dirs, ctx->P32, ctx->d_rcorr32, ctx->mut, ctx->eps, aI_n, aS_n,
+                                 ctx->d_stI + here, ctx->d_stS + here, ctx->d_Y, ctx->d_Qb, ctx->d_gA,
+                                 ctx->d_gmut, tol, ctx->desc.max_iters, ctx->d_ymax + ((lev + 1) & 1),
+                                 ctx->d_ymax + (lev & 1), ctx->d_adj_nonconv, ctx->d_adj_iters,
+                                 ctx->stream));
+      CK(mark(3, false));
+      CK(mark(4, true));
+      CK(launch_interface(ctx->n_iface, g.na, ctx->d_if_vox, ctx->d_ift_rowptr, ctx->d_ift_src,
+                          ctx->d_ift_w, ctx->d_if_keep, ctx->d_Qb, g.nv, ctx->stream));
+      CK(launch_adj_push(g, ctx->d_dirs, ctx->d_offs, ctx->d_stI, ctx->d_stS, lev_base, lev, ctx->mut,
+                         ctx->nidx, ctx->d_Qb, ctx->d_aI, ctx->d_aS, ctx->d_gmut, ctx->stream));
+      CK(mark(4, false));
+    }
+  }
+  // the forward state after the last step comes back, so stepping can continue
+  CK(mark(0, true));
+  {
+    const int rc = restore_checkpoint(ctx, nseg, N, false);
+    if (rc != TRINITY_OK) return rc;
+  }
+  CK(mark(0, false));
+  CK(mark(5, true));
+  CK(launch_adj_finish(g.nv, ctx->mut, ctx->eps, ctx->d_gA, ctx->d_gmut, ctx->d_gmua, ctx->d_gmus,
+                       ctx->stream));
+  CK(mark(5, false));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (stats) {
+    for (int ph = 0; ph < 6; ++ph) {
+      double tot = 0.0;
+      for (auto& pr : evs[ph]) {
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, pr.first, pr.second));
+        tot += ms;
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+      }
+      stats[ph] = tot;
+    }
+    unsigned long long it = 0;
+    CK(cudaMemcpy(&it, ctx->d_adj_iters, sizeof(it), cudaMemcpyDeviceToHost));
+    stats[6] = static_cast<double>(it) / (static_cast<double>(N) * static_cast<double>(nv));
+  }
+  {
+    const int rc = check_device_error(ctx);
+    if (rc != TRINITY_OK) return rc;
+  }
+  const cudaMemcpyKind kind = ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CK(cudaMemcpy(grad_mua, ctx->d_gmua, nv * sizeof(double), kind));
+  CK(cudaMemcpy(grad_mus, ctx->d_gmus, nv * sizeof(double), kind));
+  int nc = 0;
+  CK(cudaMemcpy(&nc, ctx->d_adj_nonconv, sizeof(int), cudaMemcpyDeviceToHost));
+  if (nc > 0) {
+    ctx->err = "some voxels reached max_iters in the transposed solve";
+    return TRINITY_W_NOT_CONVERGED;
+  }
+  return TRINITY_OK;
+}
+
+}  // namespace
+
+int trinity_adjoint(trinity_ctx* ctx, const double* dL_dE, size_t n, double* grad_mua, double* grad_mus,
+                    int ptr_kind) {
+  return adjoint_impl(ctx, dL_dE, n, grad_mua, grad_mus, ptr_kind, nullptr);
+}
+
+int trinity_adjoint_profile(trinity_ctx* ctx, const double* dL_dE, size_t n, double* grad_mua,
+                            double* grad_mus, int ptr_kind, double* stats) {
+  if (!stats) return ctx ? fail(ctx, TRINITY_E_INVALID, "stats is null") : TRINITY_E_INVALID;
+  return adjoint_impl(ctx, dL_dE, n, grad_mua, grad_mus, ptr_kind, stats);
+}
+
 int trinity_sync(trinity_ctx* ctx) {
   if (!ctx) return TRINITY_E_INVALID;
   CK(cudaStreamSynchronize(ctx->stream));
@@ -923,6 +1272,7 @@ int trinity_reset(trinity_ctx* ctx) {
   ctx->has_init = false;
   ctx->steps_done = 0;
   ctx->nonconv_seen = 0;
+  free_adjoint(ctx);
   if (ctx->graph) {
     cudaGraphExecDestroy(ctx->graph);
     ctx->graph = nullptr;
@@ -938,6 +1288,7 @@ const char* trinity_last_error(const trinity_ctx* ctx) {
 void trinity_destroy(trinity_ctx* ctx) {
   if (!ctx) return;
   free_interfaces(ctx);
+  free_adjoint(ctx);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   void* bufs[] = {ctx->I,         ctx->S,          ctx->Q,           ctx->mut,       ctx->eps,
                   ctx->nidx,      ctx->P32,        ctx->Pbf,         ctx->d_dirs,    ctx->d_offs,

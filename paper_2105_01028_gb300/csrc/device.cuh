@@ -141,3 +141,26 @@ cudaError_t tc_tile_selftest(int na, const uint16_t* A, const uint16_t* B, float
                              cudaStream_t st);
 
 }  // namespace trinity
+
+namespace trinity {
+
+// Adjoint launchers (defined in adjoint.cu).
+cudaError_t launch_adj_inject(const int* det_vox, const int* det_dir, const float* det_w,
+                              const int* det_id, int n_entries, const double* G, int nbins, int b,
+                              float* Ib_n, int nv, unsigned* ymax_cur, cudaStream_t st);
+cudaError_t launch_adj_scatter_fp32(const GridParams& g, const DirInfo* dirs, const float* P,
+                                    const float* rcorr, const float* mut, const float* eps,
+                                    float* Ib_n, float* Sb_n, const float* I_n, const float* S_n,
+                                    float* Y, float* Qb, double* gA, double* gmut, float tol,
+                                    int max_iters, const unsigned* yglob_prev, unsigned* ymax_cur,
+                                    int* nonconv, unsigned long long* iters_sum, cudaStream_t st);
+cudaError_t launch_adj_push(const GridParams& g, const DirInfo* dirs, const int8_t* offs,
+                            const float* stI, const float* stS, int lev_base, int n,
+                            const float* mut, const float* nidx, const float* Qb, float* IbR,
+                            float* SbR, double* gmut, cudaStream_t st);
+cudaError_t launch_adj_finish(int nv, const float* mut, const float* eps, const double* gA,
+                              const double* gmut, double* gmua, double* gmus, cudaStream_t st);
+cudaError_t launch_adj_restore(int* step, int c, unsigned* smax, const unsigned* saved,
+                               cudaStream_t st);
+
+}  // namespace trinity

@@ -150,6 +150,36 @@ def config_served(n_side_len, nside, steps, seed, sigma=0.3, corr_mm=5.0, precis
     return _bins(p)
 
 
+def config_adjoint(n=64, nside=4, steps=800, seed=11, sigma=0.3, corr_mm=5.0,
+                   precision="fp32", tol=1e-6, bump=0.2):
+    """Gradient workload: an n^3 grid at 1 mm (64^3), 192 directions, log-normal random-field
+    optics (median mu_a 0.01/mm, mu_s 10/mm, sigma 0.3, correlation length 5 mm), g 0.9,
+    n 1.4; delta pulse into a 15-degree cone at (n/4, n/2) on the -z face; 8 detectors on
+    the -z face at 10..40 mm (scaled by n/64) along +x.  Returns (prob, prob_perturbed):
+    the second has mu_a raised by ``bump`` (20 %) inside a Gaussian blob (std 4 mm, scaled)
+    at depth n/6 midway between the source and the detectors; its detector curves are the
+    observations of the least-squares misfit."""
+    p = homogeneous(n, n, n, nside, 0.01, 10.0, steps=steps, tol=tol, precision=precision)
+    rng = np.random.default_rng(seed)
+    za = gaussian_random_field((n, n, n), corr_mm * n / 64.0, 1.0, rng)
+    zs = gaussian_random_field((n, n, n), corr_mm * n / 64.0, 1.0, rng)
+    p["mua"] = (0.01 * np.exp(sigma * za)).astype(np.float32)
+    p["mus"] = (10.0 * np.exp(sigma * zs)).astype(np.float32)
+    su, sv = float(n // 4), float(n // 2)
+    p["source"] = dict(face=4, u_mm=su, v_mm=sv, half_angle_deg=15.0, pulse_steps=1, energy=1.0)
+    seps = np.linspace(10.0, 40.0, 8) * (n / 64.0)
+    p["detectors"] = [dict(face=4, u_mm=su + 0.5 + float(s), v_mm=sv + 0.5, radius_mm=0.5,
+                           half_angle_deg=15.0) for s in seps]
+    _bins(p)
+    zz, yy, xx = np.meshgrid(np.arange(n) + 0.5, np.arange(n) + 0.5, np.arange(n) + 0.5,
+                             indexing="ij")
+    cx, cy, cz, r = su + 0.5 + 12.5 * n / 64.0, sv + 0.5, n / 6.0, 4.0 * n / 64.0
+    blob = np.exp(-((xx - cx) ** 2 + (yy - cy) ** 2 + (zz - cz) ** 2) / (2 * r * r))
+    q = dict(p)
+    q["mua"] = (p["mua"] * (1.0 + bump * blob)).astype(np.float32)
+    return p, q
+
+
 def served_stream(n_requests=2000, seed=4, rate_per_s=1.0):
     """Arrival times and shapes of the served stream: Poisson arrivals, cubic N uniform on
     32..96, 48 or 192 directions with probability 1/2, 500..1500 steps."""
