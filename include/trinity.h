@@ -361,6 +361,12 @@ int trinity_interface_entries(int nside, int nx, int ny, int nz, double h_mm, in
                               const float* nmap, int* vox, int* j, int* d, double* w, size_t cap,
                               size_t* count);
 
+/* Parent of every fine direction in the HEALPix hierarchy, out[12 nside_fine^2] (RING
+ * index of the coarse pixel that contains the fine pixel's centre; Section 2.1 evaluates
+ * the source function on coarse bins from the mean of their finer bins).  nside_fine
+ * must be a multiple of nside_coarse. */
+int trinity_parent_map(int nside_fine, int nside_coarse, int* out, size_t n);
+
 /* Cone weights alpha_d (double [N_a]) of a face: the fraction of a cap of half_angle_deg
  * around the inward (inward = 1) or outward normal nearest to each direction. */
 int trinity_cone_weights(int nside, int face, double half_angle_deg, int inward, double* out,

@@ -388,6 +388,15 @@ def interface_entries(nside, nidx, h=1.0, periodic=False):
     return vox, j, d, w
 
 
+def parent_map(nside_fine, nside_coarse):
+    """Coarse RING pixel containing each fine pixel's centre (int array [12 nside_fine^2])."""
+    out = np.zeros(12 * nside_fine * nside_fine, dtype=np.int32)
+    rc = lib().trinity_parent_map(int(nside_fine), int(nside_coarse), out.ctypes.data_as(_lib.P_int), out.size)
+    if rc != OK:
+        raise TrinityError(rc, "trinity_parent_map failed")
+    return out
+
+
 def cone_weights(nside, face, half_angle_deg, inward):
     n = 12 * nside * nside
     out = np.zeros(n)

@@ -91,6 +91,7 @@ SIGNATURES = {
                                        ctypes.POINTER(ctypes.c_int32), P_double,
                                        ctypes.POINTER(ctypes.c_int8), c_size_t]),
     "trinity_cone_weights": (c_int, [c_int, c_int, c_double, c_int, P_double, c_size_t]),
+    "trinity_parent_map": (c_int, [c_int, c_int, P_int, c_size_t]),
 }
 
 _lib = None

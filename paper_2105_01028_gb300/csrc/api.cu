@@ -1401,6 +1401,18 @@ int trinity_interface_entries(int nside, int nx, int ny, int nz, double h_mm, in
   return TRINITY_OK;
 }
 
+int trinity_parent_map(int nside_fine, int nside_coarse, int* out, size_t n) {
+  if (nside_fine < 1 || nside_fine > 64 || nside_coarse < 1 || !out) return TRINITY_E_INVALID;
+  try {
+    const std::vector<int> par = parent_map(nside_fine, nside_coarse);
+    if (n != par.size()) return TRINITY_E_INVALID;
+    std::copy(par.begin(), par.end(), out);
+  } catch (...) {
+    return TRINITY_E_INVALID;
+  }
+  return TRINITY_OK;
+}
+
 int trinity_cone_weights(int nside, int face, double half_angle_deg, int inward, double* out, size_t n) {
   if (nside < 1 || nside > 64 || !out) return TRINITY_E_INVALID;
   try {

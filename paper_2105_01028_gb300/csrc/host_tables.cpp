@@ -27,6 +27,52 @@ long floor_snap(double y) {
 // hold 4i pixels at z = 1 - i^2/(3N^2), phi = (pi/2i)(j - 1/2); belt rings hold 4N
 // pixels at z = 4/3 - 2i/(3N), phi = (pi/2N)(j - s/2) with s = (i - N + 1) mod 2; the
 // southern cap mirrors the northern one.
+// RING index of the pixel containing the direction (z, phi).  HEALPix pixel boundaries
+// (Gorski et al. 2005): in the belt |z| <= 2/3 they are the lines of a square lattice
+// in (t + w/2, t - w/2) with t = 2 N phi / pi and w = 3 N z / 2; in the caps they are the
+// curves x = k and y = k with x = tp sigma, y = (1 - tp) sigma, sigma = N sqrt(3 (1 - |z|)),
+// tp the fraction of phi inside its quarter.
+long ring_pixel(int nside, double z, double phi) {
+  const double N = nside;
+  const long npix = 12L * nside * nside;
+  phi = std::fmod(phi, 2.0 * kPi);
+  if (phi < 0.0) phi += 2.0 * kPi;
+  if (std::fabs(z) <= 2.0 / 3.0) {
+    const double t = 2.0 * N * phi / kPi, w = 1.5 * N * z;
+    const double half = 0.5 * (N - 1.0);
+    // lattice cell of the point: centres at half + integers along both rotated axes
+    const long ka = static_cast<long>(std::floor(t + 0.5 * w - half + 0.5));
+    const long kb = static_cast<long>(std::floor(t - 0.5 * w - half + 0.5));
+    const long ring = 2L * nside - (ka - kb);           // a0 - b0 = ka - kb
+    const long s = ((ring - nside + 1) % 2 + 2) % 2;
+    // j = (a0 + b0 + s) / 2 with a0 + b0 = ka + kb + 2 half = ka + kb + N - 1
+    long j = (ka + kb + nside - 1 + s) / 2;
+    j = ((j - 1) % (4L * nside) + 4L * nside) % (4L * nside) + 1;
+    return 2L * nside * (nside - 1) + 4L * nside * (ring - nside) + (j - 1);
+  }
+  const double sigma = N * std::sqrt(3.0 * (1.0 - std::fabs(z)));
+  double q = std::floor(phi / (0.5 * kPi));
+  if (q > 3.0) q = 3.0;
+  const double tp = phi / (0.5 * kPi) - q;
+  const long kx = static_cast<long>(std::floor(tp * sigma));
+  const long ky = static_cast<long>(std::floor((1.0 - tp) * sigma));
+  const long ring = kx + ky + 1;  // counted from the nearer pole
+  const long j = static_cast<long>(q) * ring + kx + 1;
+  if (z > 0.0) return 2L * ring * (ring - 1) + (j - 1);
+  return npix - 2L * ring * (ring + 1) + (j - 1);
+}
+
+std::vector<int> parent_map(int nside_fine, int nside_coarse) {
+  if (nside_coarse < 1 || nside_fine % nside_coarse != 0)
+    throw std::runtime_error("the transport nside must be a multiple of the source-function nside");
+  const std::vector<double> d = healpix_dirs(nside_fine);
+  const size_t n = d.size() / 3;
+  std::vector<int> par(n);
+  for (size_t f = 0; f < n; ++f)
+    par[f] = static_cast<int>(ring_pixel(nside_coarse, d[3 * f + 2], std::atan2(d[3 * f + 1], d[3 * f])));
+  return par;
+}
+
 std::vector<double> healpix_dirs(int nside) {
   if (nside < 1) throw std::runtime_error("nside must be >= 1");
   const int npix = 12 * nside * nside;

@@ -14,6 +14,12 @@ constexpr int kRing = 5;            // stored time levels of I and S
 // HEALPix RING pixel centres (x, y, z) per direction.
 std::vector<double> healpix_dirs(int nside);
 
+// RING index of the HEALPix pixel containing direction (z = cos theta, phi).
+long ring_pixel(int nside, double z, double phi);
+
+// Coarse pixel containing each fine pixel's centre (its parent in the nested hierarchy).
+std::vector<int> parent_map(int nside_fine, int nside_coarse);
+
 // Normalised phase matrix of Eq. 12 (row-major N_a x N_a) and its g_eff.
 std::vector<double> phase_matrix(int nside, double g, double* g_eff);
 

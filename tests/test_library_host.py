@@ -123,3 +123,9 @@ def test_interface_table_matches_oracle(nside, scale, dims):
     assert set(got) == set(ref)
     for k in ref:
         assert abs(got[k] - ref[k]) <= 1e-13
+
+
+@pytest.mark.parametrize("fine,coarse", [(16, 4), (8, 4), (4, 2), (2, 1), (16, 2), (4, 4)])
+def test_parent_map_matches_oracle_exactly(fine, coarse):
+    from oracle.healpix import parent_map as oracle_parent
+    assert np.array_equal(T.parent_map(fine, coarse), oracle_parent(fine, coarse))
