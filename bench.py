@@ -208,12 +208,18 @@ class ClockSampler:
 
 def workload_config(args):
     nx, ny, nz = args.grid
-    return {"workload": "phantom-scale slab %dx%dx%d voxels @1mm, 192 HEALPix dirs (Nside 4), " % (nx, ny, nz) +
+    if args.two_level:
+        dirs = "3072 HEALPix transport dirs (Nside 16), source function on 192 (Nside 4, mean of 16 children)"
+        hist = "36 GB"
+    else:
+        dirs = "192 HEALPix dirs (Nside 4)"
+        hist = "4.5 GB"
+    return {"workload": "phantom-scale slab %dx%dx%d voxels @1mm, %s, " % (nx, ny, nz, dirs) +
                         "mu_a 0.008/mm, mu_s 8/mm, g 0.9, n 1.4, 15-deg delta pulse, 8 detectors, "
                         "10 ps bins",
             "window": "time steps %d..%d of the 1500-step solve" % (
                 args.spinup + args.warmup, args.spinup + args.warmup + args.steps - 1),
-            "tol": 1e-6, "l2": "inputs larger than L2 (4.5 GB time-level history per solve)",
+            "tol": 1e-6, "l2": "inputs larger than L2 (%s time-level history per solve)" % hist,
             "parallelism": "replicas" if dist_env()[0] > 1 else "single GPU",
             "precision": args.precision}
 
@@ -421,6 +427,8 @@ def main():
                     help="run the served stream with N requests instead of the slab")
     ap.add_argument("--rate", type=float, default=8.0, help="served stream arrival rate (1/s)")
     ap.add_argument("--slots", type=int, default=8, help="served stream concurrent slots")
+    ap.add_argument("--two-level", action="store_true",
+                    help="slab on the paper's fiducial angles: 3072 transport, 192 source-function dirs")
     ap.add_argument("--adjoint", action="store_true", help="gradient workload (checkpointed adjoint)")
     ap.add_argument("--adjoint-grid", type=int, default=64)
     ap.add_argument("--adjoint-steps", type=int, default=800)
@@ -446,10 +454,16 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     total = args.spinup + args.warmup + args.steps + 16
     nx, ny, nz = args.grid
-    prob = W.config_slab(steps=total, precision=args.precision, nx=nx, ny=ny, nz=nz)
+    if args.two_level:
+        prob = W.config_slab(steps=total, precision=args.precision, nx=nx, ny=ny, nz=nz, nside=16)
+        prob["nside_scatter"] = 4
+    else:
+        prob = W.config_slab(steps=total, precision=args.precision, nx=nx, ny=ny, nz=nz)
     stream = torch.cuda.Stream()
     nv = prob["nx"] * prob["ny"] * prob["nz"]
-    na = 12 * prob["nside"] ** 2
+    na = 12 * prob["nside"] ** 2          # transport directions (updates are counted on these)
+    na_s = 12 * (prob.get("nside_scatter") or prob["nside"]) ** 2  # source-function directions
+    nch = na // na_s
 
     # ---- e2e job through the public API, from host buffers: optics upload, spin-up,
     # warm-up and the timed window, per-step tallies and detector curves read back.
@@ -497,9 +511,15 @@ def main():
     value = ws * updates / (ms * 1e-3)
     pk = peaks()
     hbm = pk["hbm_gbs"]
-    sweep_bytes = nv * na * 20 + nv * 8  # I,S at two levels read (16 B), Q written (4 B); optics
-    scat_bytes = nv * na * 16 + nv * 12  # Q, S(n-1) read, I, S written; optics
-    scat_flops = 2.0 * na * na * nv * k_mean  # angular sum per voxel per iteration
+    if nch == 1:
+        sweep_bytes = nv * na * 20 + nv * 8  # I,S at two levels read (16 B), Q written (4 B); optics
+    else:
+        # fine I at two levels (8 B) and Q written (4 B) per fine update; coarse S at two
+        # levels and the coarse mean Q once per coarse update
+        sweep_bytes = nv * na * 12 + nv * na_s * 12 + nv * 8
+    fin_bytes = nv * na * 8 + nv * na_s * 4 if nch > 1 else 0  # refine: Q_f in, I_f out, S_c in
+    scat_bytes = nv * na_s * 16 + nv * 12  # Q, S(n-1) read, I, S written; optics
+    scat_flops = 2.0 * na_s * na_s * nv * k_mean  # angular sum per voxel per iteration
     per = [kms[0] / kp, kms[1] / kp, kms[2] / kp]
     tot = sum(per)
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
@@ -512,15 +532,24 @@ def main():
     kernels = [
         {"name": "sweep", "ms": per[0], "share": per[0] / tot, "bound": "hbm",
          "achieved": w_ach, "peak": hbm, "unit": "GB/s", "frac": w_ach / hbm,
-         "algorithmic_bytes": sweep_bytes, "traffic": measured_traffic("sweep_kernel", nv * na)},
+         "algorithmic_bytes": sweep_bytes,
+         "traffic": measured_traffic("sweep2_kernel" if nch > 1 else "sweep_kernel", nv * na)},
         {"name": "scatter_" + args.precision, "ms": per[1], "share": per[1] / tot,
          "bound": s_bound, "achieved": s_ach, "peak": s_peak, "unit": s_unit,
          "frac": s_ach / s_peak, "algorithmic_flops": scat_flops,
          "hbm_gbs": scat_bytes / (per[1] * 1e-3) / 1e9},
         {"name": "tally+advance", "ms": per[2], "share": per[2] / tot},
     ]
+    if nch > 1:
+        f_ach = fin_bytes / (per[2] * 1e-3) / 1e9
+        kernels[0]["name"] = "sweep2 (fused coarse mean)"
+        kernels[2] = {"name": "refine+tally+advance", "ms": per[2], "share": per[2] / tot, "bound": "hbm",
+                      "achieved": f_ach, "peak": hbm, "unit": "GB/s", "frac": f_ach / hbm,
+                      "algorithmic_bytes": fin_bytes}
     dom = max(kernels[:2], key=lambda k: k["ms"])
-    traffic = measured_traffic("scatter_tc_kernel", nv * na) if dom["name"] == "scatter_bf16" else None
+    traffic = (measured_traffic("scatter_tc_kernel", nv * na_s) if dom["name"] == "scatter_bf16"
+               else measured_traffic("sweep2_kernel" if nch > 1 else "sweep_kernel", nv * na)
+               if dom is kernels[0] else None)
     roof = {"kernel": dom["name"], "bound": dom["bound"], "achieved": dom["achieved"],
             "peak": dom["peak"], "unit": dom["unit"], "frac": dom["frac"], "traffic": traffic,
             "peak_source": pk["_source"] + (" (FP32 FFMA: 152 SMs x 128 lanes x 2 x max SM clock)"
@@ -531,7 +560,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16-scatter/f32-sweep" if args.precision == "bf16" else "f32",
             "data": "synthetic", "config": workload_config(args),
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": (5 if nch > 1 else 4) * args.steps,
             "iterations": {"mean": float(np.mean(win_mean)), "max": int(np.max(win_max))},
             "status": int(status),
             "roofline": roof, "kernels": kernels, "clocks": clk.summary(),
@@ -556,7 +585,10 @@ def main():
         line["fp32"] = {"value": ws * updates / (m32 * 1e-3), "ms_per_step": m32 / args.steps}
         f32.close()
 
-    if rank == 0 and not args.no_cpu and ws >= 1:
+    if args.two_level:
+        line["cpu_baseline"] = None
+        line["cpu_baseline_note"] = "the timed oracle leg samples the one-level step only"
+    if rank == 0 and not args.no_cpu and ws >= 1 and not args.two_level:
         v, info = CpuLeg(prob).sample(args.cpu_voxels, seed=100)
         line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": cpu_cores(),
                                 "kind": "oracle",

@@ -57,7 +57,8 @@ enum { TRINITY_FIELD_I = 0, TRINITY_FIELD_S = 1 };
 /*
  * Grid and solver description.
  *   nx, ny, nz   voxels per axis (>= 2 each); h_mm voxel size.
- *   nside        HEALPix resolution: 1, 2 or 4 (12, 48, 192 directions).
+ *   nside        HEALPix resolution of the transport: 1, 2 or 4 (12, 48, 192 directions);
+ *                up to 16 (3072) with a coarser nside_scatter.
  *   courant      c0 * dt / (n_ref * h): the time step dt = courant * h * n_ref / c0
  *                (the paper's rule "dt = fraction x light-crossing time of a grid",
  *                Sections 2.2 and 3.1).
@@ -68,6 +69,16 @@ enum { TRINITY_FIELD_I = 0, TRINITY_FIELD_S = 1 };
  *                cores; transport FP32; detector and energy sums FP64 in both modes).
  *   tol          source-iteration tolerance (relative, see trinity_step).
  *   max_iters    source-iteration cap per step (>= 1).
+ *   nside_scatter  0 (or nside): one angular grid.  Otherwise the source function lives
+ *                on the coarser HEALPix grid nside_scatter (1, 2 or 4) while the transport
+ *                runs on nside (2, 4, 8 or 16, a multiple): each coarse bin takes the mean
+ *                intensity of its (nside / nside_scatter)^2 finer bins, as the paper's
+ *                fiducial runs do with 3072 transport and 192 source-function bins
+ *                (Section 2.1, text after Eq. 12).  Per step the sweep forms Q on the fine
+ *                directions and its mean over each coarse bin's children, the source
+ *                iteration runs on the coarse bins with b1 the children's mean b1, and
+ *                I = Q + b1 S(parent) is formed on the fine directions.  Fields: I has
+ *                12 nside^2 directions, S 12 nside_scatter^2.  No adjoint on two levels.
  */
 typedef struct {
   int nx, ny, nz;
@@ -79,6 +90,7 @@ typedef struct {
   int precision;
   double tol;
   int max_iters;
+  int nside_scatter;
 } trinity_grid_desc;
 
 /* Bytes of device memory a context with this description allocates (for admission

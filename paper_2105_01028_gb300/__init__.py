@@ -31,7 +31,8 @@ def grid_desc(prob):
     return GridDesc(int(prob["nx"]), int(prob["ny"]), int(prob["nz"]), float(prob["h"]),
                     int(prob["nside"]), float(prob["courant"]), float(prob["n_ref"]),
                     _BOUND[prob.get("boundary", "vacuum")], _PREC[prob.get("precision", "fp32")],
-                    float(prob.get("tol", 1e-6)), int(prob.get("max_iters", 2000)))
+                    float(prob.get("tol", 1e-6)), int(prob.get("max_iters", 2000)),
+                    int(prob.get("nside_scatter") or 0))
 
 
 def footprint_bytes(prob):
@@ -76,6 +77,8 @@ class Forward:
         self.h = h
         self.nv = desc.nx * desc.ny * desc.nz
         self.na = 12 * desc.nside * desc.nside
+        ns = desc.nside_scatter or desc.nside
+        self.na_s = 12 * ns * ns  # directions of S (coarser on a two-level angular grid)
         self._check(self.set_optics(prob["mua"], prob["mus"], prob["nidx"], prob["g"]))
         if prob.get("fresnel", False):
             self._check(self.L.trinity_set_fresnel(self.h, 1))
@@ -236,12 +239,13 @@ class Forward:
         return mx, mean
 
     def field(self, what=FIELD_I, back=0, out=None):
-        """Field at level steps_done-1-back as a host array [N_a, N_v] (or into a CUDA tensor)."""
+        """Field at level steps_done-1-back as a host array [N_a, N_v] (or into a CUDA tensor);
+        S has the source function's N_a (coarser on a two-level angular grid)."""
         if out is not None and getattr(out, "is_cuda", False):
             self._check(self.L.trinity_read_field(self.h, what, back, ctypes.c_void_p(out.data_ptr()),
                                                   out.numel() * 4, 1))
             return out
-        arr = np.empty((self.na, self.nv), dtype=np.float32)
+        arr = np.empty((self.na_s if what == FIELD_S else self.na, self.nv), dtype=np.float32)
         self._check(self.L.trinity_read_field(self.h, what, back, arr.ctypes.data_as(ctypes.c_void_p),
                                               arr.nbytes, 0))
         return arr

@@ -23,7 +23,7 @@ class GridDesc(ctypes.Structure):
     _fields_ = [("nx", c_int), ("ny", c_int), ("nz", c_int), ("h_mm", c_double),
                 ("nside", c_int), ("courant", c_double), ("n_ref", c_double),
                 ("boundary", c_int), ("precision", c_int), ("tol", c_double),
-                ("max_iters", c_int)]
+                ("max_iters", c_int), ("nside_scatter", c_int)]
 
 
 class SourceDesc(ctypes.Structure):

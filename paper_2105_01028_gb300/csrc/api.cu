@@ -76,6 +76,16 @@ struct trinity_ctx {
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
 
+  // two-level angular grid: S on na_s coarse directions, each the mean of nch children
+  int na_s = 0;              // directions of S (= g.na on one grid)
+  int nch = 1;               // children per coarse direction (1 on one grid)
+  bool two_level = false;
+  GridParams g_s{};          // the scatter's view: na = na_s, energy weight of a coarse bin
+  int* d_children = nullptr; // [na_s][nch] fine directions of each coarse one (ascending)
+  float* d_b1ds = nullptr;   // [na_s][nch] ray spacings whose b1 the scatter averages
+  float* Qc = nullptr;       // [na_s][N_v] mean Q over each coarse bin's children
+  float* Ic = nullptr;       // [5][na_s][N_v] coarse mean intensity (written by the scatter)
+
   // index interfaces (Eqs. 13-14)
   bool fresnel = false;
   std::vector<float> nmap;  // host copy of the refractive-index map
@@ -143,8 +153,16 @@ bool desc_valid(const trinity_grid_desc* d, std::string* why) {
     *why = "h_mm, courant must be > 0 and n_ref >= 1";
     return false;
   }
-  if (d->nside != 1 && d->nside != 2 && d->nside != 4) {
-    *why = "nside must be 1, 2 or 4";
+  const int ns = d->nside_scatter == 0 ? d->nside : d->nside_scatter;
+  if (ns == d->nside) {
+    if (d->nside != 1 && d->nside != 2 && d->nside != 4) {
+      *why = "nside must be 1, 2 or 4";
+      return false;
+    }
+  } else if ((ns != 1 && ns != 2 && ns != 4) ||
+             (d->nside != 2 && d->nside != 4 && d->nside != 8 && d->nside != 16) ||
+             d->nside % ns != 0 || d->nside < ns || (d->nside / ns) * (d->nside / ns) > 64) {
+    *why = "two-level grid: nside_scatter 1, 2 or 4 and nside 2..16 a multiple of it";
     return false;
   }
   if (d->boundary != TRINITY_BOUNDARY_VACUUM && d->boundary != TRINITY_BOUNDARY_PERIODIC) {
@@ -165,11 +183,15 @@ bool desc_valid(const trinity_grid_desc* d, std::string* why) {
 size_t footprint(const trinity_grid_desc* d) {
   const size_t nv = static_cast<size_t>(d->nx) * d->ny * d->nz;
   const size_t na = 12u * d->nside * d->nside;
+  const int nsc = d->nside_scatter == 0 ? d->nside : d->nside_scatter;
+  const size_t na_s = 12u * nsc * nsc;
   size_t b = 0;
-  b += 2 * kRing * na * nv * sizeof(float);  // I, S history
-  b += na * nv * sizeof(float);              // Q
-  b += 3 * nv * sizeof(float);               // optics
-  b += na * na * (sizeof(float) + sizeof(uint16_t));
+  b += kRing * na * nv * sizeof(float);        // I history
+  b += kRing * na_s * nv * sizeof(float);      // S history
+  b += na * nv * sizeof(float);                // Q
+  if (na_s != na) b += (kRing + 1) * na_s * nv * sizeof(float);  // coarse I history, Qbar
+  b += 3 * nv * sizeof(float);                 // optics
+  b += na_s * na_s * (sizeof(float) + sizeof(uint16_t));
   return b;
 }
 
@@ -287,6 +309,7 @@ BfTables bf_tables(trinity_ctx* c) {
   t.cls = c->d_cls;
   t.cls_ds = c->d_cls_ds;
   t.ncls = c->ncls;
+  t.nch = c->nch;
   return t;
 }
 
@@ -429,27 +452,59 @@ int restore_checkpoint(trinity_ctx* ctx, int k, int c, bool store) {
   return TRINITY_OK;
 }
 
-// The launches of one time step (all on ctx->stream; the step index lives on the device).
-// ``rs`` and ``det`` take the step's tallies.
-int enqueue_step_with(trinity_ctx* ctx, const RunState& rs, double* det) {
+// Sweep (Eq. 10's known part Q) and the interface split; on a two-level grid also the
+// mean of Q over each coarse direction's children.
+int enqueue_transport(trinity_ctx* ctx, const RunState& rs) {
   const GridParams& g = ctx->g;
-  CK(launch_sweep(g, ctx->d_dirs, ctx->d_offs, ctx->I, ctx->S, ctx->mut, ctx->nidx, ctx->Q, rs,
-                  ctx->stream));
+  if (ctx->two_level) {
+    CK(launch_sweep2(g, ctx->d_dirs, ctx->d_offs, ctx->d_children, ctx->nch, ctx->na_s, ctx->I, ctx->S,
+                     ctx->mut, ctx->nidx, ctx->Q, ctx->Qc, rs, ctx->stream));
+  } else {
+    CK(launch_sweep(g, ctx->d_dirs, ctx->d_offs, ctx->I, ctx->S, ctx->mut, ctx->nidx, ctx->Q, rs,
+                    ctx->stream));
+  }
   CK(launch_interface(ctx->n_iface, g.na, ctx->d_if_vox, ctx->d_if_rowptr, ctx->d_if_src, ctx->d_if_w,
                       ctx->d_if_keep, ctx->Q, g.nv, ctx->stream));
+  if (ctx->two_level)
+    CK(launch_recoarsen(ctx->n_iface, ctx->d_if_vox, ctx->d_children, ctx->nch, ctx->na_s, ctx->Q, ctx->Qc,
+                        g.nv, ctx->stream));
+  return TRINITY_OK;
+}
+
+// The per-voxel source iteration (Eq. 12) on the source function's directions.
+int enqueue_scatter(trinity_ctx* ctx, const RunState& rs) {
+  const GridParams& gs = ctx->g_s;
   if (ctx->desc.precision == TRINITY_BF16) {
-    CK(launch_scatter_bf16(g, bf_tables(ctx), ctx->Pbf, ctx->Q, ctx->mut, ctx->eps, ctx->nidx, ctx->I,
+    CK(launch_scatter_bf16(gs, bf_tables(ctx), ctx->Pbf, ctx->Qc, ctx->mut, ctx->eps, ctx->nidx, ctx->Ic,
                            ctx->S, static_cast<float>(ctx->desc.tol), ctx->desc.max_iters, rs,
                            ctx->stream));
   } else {
-    CK(launch_scatter_fp32(g, ctx->d_dirs, ctx->P32, ctx->d_rcorr32, ctx->Q, ctx->mut, ctx->eps, ctx->nidx, ctx->I,
-                           ctx->S, static_cast<float>(ctx->desc.tol), ctx->desc.max_iters, rs,
-                           ctx->stream));
+    CK(launch_scatter_fp32(gs, ctx->d_b1ds, ctx->nch, ctx->P32, ctx->d_rcorr32, ctx->Qc, ctx->mut, ctx->eps,
+                           ctx->nidx, ctx->Ic, ctx->S, static_cast<float>(ctx->desc.tol), ctx->desc.max_iters,
+                           rs, ctx->stream));
   }
+  return TRINITY_OK;
+}
+
+// I on the transport directions (two-level grid), the tallies and the step counter.
+int enqueue_finish(trinity_ctx* ctx, const RunState& rs, double* det) {
+  const GridParams& g = ctx->g;
+  if (ctx->two_level)
+    CK(launch_refine(g, ctx->d_dirs, ctx->d_children, ctx->nch, ctx->na_s, ctx->mut, ctx->Q, ctx->S, ctx->I,
+                     rs, ctx->stream));
   CK(launch_tally(g, ctx->d_dirs, ctx->I, ctx->d_det_vox, ctx->d_det_dir, ctx->d_det_w,
                   ctx->d_det_id, ctx->n_det_entries, det, ctx->nbins, rs, ctx->stream));
   CK(launch_advance(rs, ctx->stream));
   return TRINITY_OK;
+}
+
+// The launches of one time step (all on ctx->stream; the step index lives on the device).
+// ``rs`` and ``det`` take the step's tallies.
+int enqueue_step_with(trinity_ctx* ctx, const RunState& rs, double* det) {
+  int rc = enqueue_transport(ctx, rs);
+  if (rc == TRINITY_OK) rc = enqueue_scatter(ctx, rs);
+  if (rc == TRINITY_OK) rc = enqueue_finish(ctx, rs, det);
+  return rc;
 }
 
 int enqueue_step(trinity_ctx* ctx) { return enqueue_step_with(ctx, run_state(ctx), ctx->d_det); }
@@ -500,7 +555,8 @@ int trinity_create_grid(const trinity_grid_desc* desc, void* cuda_stream, trinit
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, ctx->device) != cudaSuccess) return bail(TRINITY_E_CUDA);
   if (!(prop.major == 10 && prop.minor == 3)) return bail(TRINITY_E_UNSUPPORTED);
-  if (desc->precision == TRINITY_BF16 && !scatter_bf16_supported(12 * desc->nside * desc->nside))
+  const int nside_s = desc->nside_scatter == 0 ? desc->nside : desc->nside_scatter;
+  if (desc->precision == TRINITY_BF16 && !scatter_bf16_supported(12 * nside_s * nside_s))
     return bail(TRINITY_E_UNSUPPORTED);
 
   GridParams& g = ctx->g;
@@ -549,40 +605,89 @@ int trinity_create_grid(const trinity_grid_desc* desc, void* cuda_stream, trinit
   }
   g.ds_max = static_cast<float>(dsmax);
 
-  const size_t nv = g.nv, na = g.na;
-  if (dalloc(&ctx->I, kRing * na * nv) != cudaSuccess || dalloc(&ctx->S, kRing * na * nv) != cudaSuccess ||
+  // angular grids: S and the source iteration on na_s directions; on a two-level grid
+  // each coarse direction c owns the nch fine directions whose centres it contains
+  ctx->na_s = 12 * nside_s * nside_s;
+  ctx->two_level = ctx->na_s != g.na;
+  std::vector<int> children;   // [na_s][nch]
+  std::vector<float> b1ds;     // [na_s][nch]
+  if (ctx->two_level) {
+    std::vector<int> par;
+    try {
+      par = parent_map(desc->nside, nside_s);
+    } catch (const std::exception&) {
+      return bail(TRINITY_E_INVALID);
+    }
+    ctx->nch = g.na / ctx->na_s;
+    std::vector<int> fill(ctx->na_s, 0);
+    children.assign(static_cast<size_t>(ctx->na_s) * ctx->nch, -1);
+    for (int f = 0; f < g.na; ++f) {  // ascending fine index within each coarse bin
+      const int c = par[f];
+      if (fill[c] >= ctx->nch) return bail(TRINITY_E_INVALID);
+      children[static_cast<size_t>(c) * ctx->nch + fill[c]++] = f;
+    }
+  } else {
+    ctx->nch = 1;
+    children.resize(g.na);
+    for (int d = 0; d < g.na; ++d) children[d] = d;
+  }
+  b1ds.resize(children.size());
+  for (size_t k = 0; k < children.size(); ++k) b1ds[k] = static_cast<float>(ctx->lat.ds[children[k]]);
+  ctx->g_s = g;
+  ctx->g_s.na = ctx->na_s;
+  ctx->g_s.e_scale = static_cast<float>(desc->h_mm * desc->h_mm * desc->h_mm / kC0 *
+                                        (4.0 * 3.14159265358979323846 / ctx->na_s));
+
+  const size_t nv = g.nv, na = g.na, na_s = ctx->na_s;
+  if (dalloc(&ctx->I, kRing * na * nv) != cudaSuccess || dalloc(&ctx->S, kRing * na_s * nv) != cudaSuccess ||
       dalloc(&ctx->Q, na * nv) != cudaSuccess || dalloc(&ctx->mut, nv) != cudaSuccess ||
       dalloc(&ctx->eps, nv) != cudaSuccess || dalloc(&ctx->nidx, nv) != cudaSuccess ||
-      dalloc(&ctx->P32, na * na) != cudaSuccess || dalloc(&ctx->Pbf, na * na) != cudaSuccess ||
+      dalloc(&ctx->P32, na_s * na_s) != cudaSuccess || dalloc(&ctx->Pbf, na_s * na_s) != cudaSuccess ||
       dalloc(&ctx->d_dirs, na) != cudaSuccess ||
       dalloc(&ctx->d_offs, ctx->lat.off.size()) != cudaSuccess || dalloc(&ctx->d_step, 1) != cudaSuccess ||
       dalloc(&ctx->d_smax, 2) != cudaSuccess || dalloc(&ctx->d_nonconv, 1) != cudaSuccess ||
       dalloc(&ctx->d_error, 1) != cudaSuccess || dalloc(&ctx->d_tile_ctr, 2) != cudaSuccess ||
-      dalloc(&ctx->d_rcorr, na) != cudaSuccess || dalloc(&ctx->d_rcorr32, na) != cudaSuccess ||
-      dalloc(&ctx->d_cls, na) != cudaSuccess ||
-      dalloc(&ctx->d_cls_ds, 16) != cudaSuccess) {
+      dalloc(&ctx->d_rcorr, na_s) != cudaSuccess || dalloc(&ctx->d_rcorr32, na_s) != cudaSuccess ||
+      dalloc(&ctx->d_cls, na_s) != cudaSuccess || dalloc(&ctx->d_cls_ds, 16 * ctx->nch) != cudaSuccess ||
+      dalloc(&ctx->d_children, children.size()) != cudaSuccess ||
+      dalloc(&ctx->d_b1ds, b1ds.size()) != cudaSuccess ||
+      (ctx->two_level && (dalloc(&ctx->Qc, na_s * nv) != cudaSuccess ||
+                          dalloc(&ctx->Ic, kRing * na_s * nv) != cudaSuccess))) {
     cudaGetLastError();
     return bail(TRINITY_E_OOM);
   }
+  if (!ctx->two_level) {
+    ctx->Qc = ctx->Q;  // one grid: the scatter reads Q and writes I directly
+    ctx->Ic = ctx->I;
+  }
   if (cudaMemcpy(ctx->d_offs, ctx->lat.off.data(), ctx->lat.off.size(), cudaMemcpyHostToDevice) !=
-      cudaSuccess)
+          cudaSuccess ||
+      cudaMemcpy(ctx->d_children, children.data(), children.size() * sizeof(int), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(ctx->d_b1ds, b1ds.data(), b1ds.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
     return bail(TRINITY_E_CUDA);
   {
-    // classes of equal ray-sample spacing (the tensor-core kernel tabulates b1 per class)
-    std::vector<uint8_t> cls(g.na);
-    std::vector<float> cds;
-    for (int d = 0; d < g.na; ++d) {
-      const float ds = static_cast<float>(ctx->lat.ds[d]);
-      int k = 0;
-      while (k < static_cast<int>(cds.size()) && cds[k] != ds) ++k;
-      if (k == static_cast<int>(cds.size())) cds.push_back(ds);
-      cls[d] = static_cast<uint8_t>(k < 255 ? k : 255);
+    // classes of equal ray-sample spacing (the tensor-core kernel tabulates b1 per class);
+    // on a two-level grid a class is the list of a coarse direction's children spacings
+    const int nch = ctx->nch;
+    std::vector<uint8_t> cls(na_s);
+    std::vector<std::vector<float>> cds;
+    for (size_t c = 0; c < na_s; ++c) {
+      std::vector<float> key(b1ds.begin() + c * nch, b1ds.begin() + (c + 1) * nch);
+      std::sort(key.begin(), key.end());
+      size_t k = 0;
+      while (k < cds.size() && cds[k] != key) ++k;
+      if (k == cds.size()) cds.push_back(key);
+      cls[c] = static_cast<uint8_t>(k < 255 ? k : 255);
     }
     ctx->ncls = static_cast<int>(cds.size());
     if (desc->precision == TRINITY_BF16 && ctx->ncls > 16) return bail(TRINITY_E_UNSUPPORTED);
-    cds.resize(16, 0.0f);
-    if (cudaMemcpy(ctx->d_cls, cls.data(), g.na, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(ctx->d_cls_ds, cds.data(), 16 * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+    std::vector<float> flat(16 * static_cast<size_t>(nch), 0.0f);
+    for (size_t k = 0; k < cds.size() && k < 16; ++k)
+      std::copy(cds[k].begin(), cds[k].end(), flat.begin() + k * nch);
+    if (cudaMemcpy(ctx->d_cls, cls.data(), na_s, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ctx->d_cls_ds, flat.data(), flat.size() * sizeof(float), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
       return bail(TRINITY_E_CUDA);
   }
   if (trinity_reset(ctx) != TRINITY_OK) return bail(TRINITY_E_CUDA);
@@ -629,7 +734,7 @@ int trinity_set_optics(trinity_ctx* ctx, const float* mua, const float* mus, con
                 "retarded delay outside [1, 4) steps: choose courant so that c dt < h |Omega_dom|");
   std::vector<double> P;
   try {
-    P = phase_matrix(ctx->desc.nside, g, nullptr);
+    P = phase_matrix(ctx->desc.nside_scatter == 0 ? ctx->desc.nside : ctx->desc.nside_scatter, g, nullptr);
   } catch (const std::exception& e) {
     return fail(ctx, TRINITY_E_INVALID, e.what());
   }
@@ -640,7 +745,7 @@ int trinity_set_optics(trinity_ctx* ctx, const float* mua, const float* mus, con
     Pb[k] = to_bf16(P32[k]);
   }
   // diagonal correction that gives bf16(P) + diag(r) unit row and column sums
-  const int na = ctx->g.na;
+  const int na = ctx->na_s;
   std::vector<float> rc(na);
   for (int i = 0; i < na; ++i) {
     double rs = 0.0;
@@ -808,14 +913,14 @@ int trinity_set_initial_state(trinity_ctx* ctx, const float* I0, const float* S0
   if (ctx->locked || ctx->steps_done > 0) return fail(ctx, TRINITY_E_STATE, "initial state must precede the first step");
   if (!I0 || !S0 || (ptr_kind != 0 && ptr_kind != 1)) return fail(ctx, TRINITY_E_INVALID, "bad initial state");
   const size_t cnt = static_cast<size_t>(ctx->g.na) * ctx->g.nv;
+  const size_t cnt_s = static_cast<size_t>(ctx->na_s) * ctx->g.nv;
   const cudaMemcpyKind kind = ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   for (int lev = -(kRing - 1); lev < 0; ++lev) {
-    const size_t off = static_cast<size_t>(ring_slot(lev)) * cnt;
-    CK(cudaMemcpy(ctx->I + off, I0, cnt * 4, kind));
-    CK(cudaMemcpy(ctx->S + off, S0, cnt * 4, kind));
+    CK(cudaMemcpy(ctx->I + static_cast<size_t>(ring_slot(lev)) * cnt, I0, cnt * 4, kind));
+    CK(cudaMemcpy(ctx->S + static_cast<size_t>(ring_slot(lev)) * cnt_s, S0, cnt_s * 4, kind));
   }
-  std::vector<float> hs(cnt);
-  CK(cudaMemcpy(hs.data(), S0, cnt * 4, ptr_kind ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+  std::vector<float> hs(cnt_s);
+  CK(cudaMemcpy(hs.data(), S0, cnt_s * 4, ptr_kind ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
   float m = 0.0f;
   for (float x : hs) m = std::max(m, std::fabs(x));
   unsigned bits;
@@ -902,29 +1007,19 @@ int trinity_profile_steps(trinity_ctx* ctx, int nsteps, double* kernel_ms) {
   rc = ensure_capacity(ctx, ctx->steps_done + nsteps);
   if (rc != TRINITY_OK) return rc;
   const RunState rs = run_state(ctx);
-  const GridParams& g = ctx->g;
   std::vector<cudaEvent_t> ev(4 * static_cast<size_t>(nsteps));
   for (auto& e : ev) CK(cudaEventCreate(&e));
   for (int s = 0; s < nsteps; ++s) {
     cudaEvent_t* e = &ev[4 * static_cast<size_t>(s)];
     CK(cudaEventRecord(e[0], ctx->stream));
-    CK(launch_sweep(g, ctx->d_dirs, ctx->d_offs, ctx->I, ctx->S, ctx->mut, ctx->nidx, ctx->Q, rs,
-                    ctx->stream));
-    CK(launch_interface(ctx->n_iface, g.na, ctx->d_if_vox, ctx->d_if_rowptr, ctx->d_if_src, ctx->d_if_w,
-                        ctx->d_if_keep, ctx->Q, g.nv, ctx->stream));
+    rc = enqueue_transport(ctx, rs);
+    if (rc != TRINITY_OK) return rc;
     CK(cudaEventRecord(e[1], ctx->stream));
-    if (ctx->desc.precision == TRINITY_BF16)
-      CK(launch_scatter_bf16(g, bf_tables(ctx), ctx->Pbf, ctx->Q, ctx->mut, ctx->eps, ctx->nidx, ctx->I,
-                             ctx->S, static_cast<float>(ctx->desc.tol), ctx->desc.max_iters, rs,
-                             ctx->stream));
-    else
-      CK(launch_scatter_fp32(g, ctx->d_dirs, ctx->P32, ctx->d_rcorr32, ctx->Q, ctx->mut, ctx->eps, ctx->nidx, ctx->I,
-                             ctx->S, static_cast<float>(ctx->desc.tol), ctx->desc.max_iters, rs,
-                             ctx->stream));
+    rc = enqueue_scatter(ctx, rs);
+    if (rc != TRINITY_OK) return rc;
     CK(cudaEventRecord(e[2], ctx->stream));
-    CK(launch_tally(g, ctx->d_dirs, ctx->I, ctx->d_det_vox, ctx->d_det_dir, ctx->d_det_w,
-                    ctx->d_det_id, ctx->n_det_entries, ctx->d_det, ctx->nbins, rs, ctx->stream));
-    CK(launch_advance(rs, ctx->stream));
+    rc = enqueue_finish(ctx, rs, ctx->d_det);
+    if (rc != TRINITY_OK) return rc;
     CK(cudaEventRecord(e[3], ctx->stream));
   }
   ctx->steps_done += nsteps;
@@ -953,6 +1048,8 @@ size_t trinity_adjoint_footprint_bytes(const trinity_grid_desc* desc, int nsteps
 int trinity_run_checkpointed(trinity_ctx* ctx, int nsteps, int every) {
   if (!ctx) return TRINITY_E_INVALID;
   if (nsteps < 1 || every < 1) return fail(ctx, TRINITY_E_INVALID, "nsteps and every must be >= 1");
+  if (ctx->two_level)
+    return fail(ctx, TRINITY_E_UNSUPPORTED, "the adjoint covers one angular grid (nside_scatter = nside)");
   if (ctx->steps_done != 0)
     return fail(ctx, TRINITY_E_STATE, "a checkpointed run starts at step 0 (call trinity_reset)");
   int rc = lock_inputs(ctx);
@@ -1224,7 +1321,7 @@ int trinity_read_iterations(trinity_ctx* ctx, int* iters_max, double* iters_mean
 
 int trinity_read_field(trinity_ctx* ctx, int what, int back, void* out, size_t bytes, int ptr_kind) {
   if (!ctx) return TRINITY_E_INVALID;
-  const size_t cnt = static_cast<size_t>(ctx->g.na) * ctx->g.nv;
+  const size_t cnt = static_cast<size_t>(what == TRINITY_FIELD_S ? ctx->na_s : ctx->g.na) * ctx->g.nv;
   if ((what != TRINITY_FIELD_I && what != TRINITY_FIELD_S) || back < 0 || back > kRing - 1 ||
       bytes != cnt * 4 || !out || (ptr_kind != 0 && ptr_kind != 1))
     return fail(ctx, TRINITY_E_INVALID, "bad field request");
@@ -1252,10 +1349,15 @@ int trinity_steps_done(const trinity_ctx* ctx, int* n) {
 int trinity_reset(trinity_ctx* ctx) {
   if (!ctx) return TRINITY_E_INVALID;
   const size_t cnt = static_cast<size_t>(ctx->g.na) * ctx->g.nv;
+  const size_t cnt_s = static_cast<size_t>(ctx->na_s) * ctx->g.nv;
   CK(cudaStreamSynchronize(ctx->stream));
   CK(cudaMemset(ctx->I, 0, kRing * cnt * 4));
-  CK(cudaMemset(ctx->S, 0, kRing * cnt * 4));
+  CK(cudaMemset(ctx->S, 0, kRing * cnt_s * 4));
   CK(cudaMemset(ctx->Q, 0, cnt * 4));
+  if (ctx->two_level) {
+    CK(cudaMemset(ctx->Ic, 0, kRing * cnt_s * 4));
+    CK(cudaMemset(ctx->Qc, 0, cnt_s * 4));
+  }
   CK(cudaMemset(ctx->d_step, 0, sizeof(int)));
   CK(cudaMemset(ctx->d_smax, 0, 2 * sizeof(unsigned)));
   CK(cudaMemset(ctx->d_nonconv, 0, sizeof(int)));
@@ -1289,6 +1391,12 @@ void trinity_destroy(trinity_ctx* ctx) {
   if (!ctx) return;
   free_interfaces(ctx);
   free_adjoint(ctx);
+  if (ctx->two_level) {
+    cudaFree(ctx->Qc);
+    cudaFree(ctx->Ic);
+  }
+  cudaFree(ctx->d_children);
+  cudaFree(ctx->d_b1ds);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   void* bufs[] = {ctx->I,         ctx->S,          ctx->Q,           ctx->mut,       ctx->eps,
                   ctx->nidx,      ctx->P32,        ctx->Pbf,         ctx->d_dirs,    ctx->d_offs,

@@ -50,8 +50,9 @@ struct RunState {
 struct BfTables {
   const float* rcorr;    // [na] 1 - row sum of bf16(P): diagonal correction (FP32)
   const uint8_t* cls;    // [na] class of each direction's sample spacing ds
-  const float* cls_ds;   // [ncls] ds of each class
+  const float* cls_ds;   // [ncls][nch] spacings of each class (b1 = mean of their b1)
   int ncls;              // <= 16
+  int nch;               // 1, or the children per coarse direction on a two-level grid
 };
 
 __host__ __device__ inline int ring_slot(int level) { return ((level % 5) + 5) % 5; }
@@ -120,7 +121,7 @@ __device__ __forceinline__ float ray_b1(float x, float T) {
 cudaError_t launch_sweep(const GridParams& g, const DirInfo* dirs, const int8_t* offs,
                          const float* Iring, const float* Sring, const float* mut,
                          const float* nidx, float* Q, RunState rs, cudaStream_t st);
-cudaError_t launch_scatter_fp32(const GridParams& g, const DirInfo* dirs, const float* P,
+cudaError_t launch_scatter_fp32(const GridParams& g, const float* b1ds, int nch, const float* P,
                                 const float* rcorr, const float* Q, const float* mut,
                                 const float* eps,
                                 const float* nidx, float* Iring, float* Sring, float tol,
@@ -162,5 +163,19 @@ cudaError_t launch_adj_finish(int nv, const float* mut, const float* eps, const 
                               const double* gmut, double* gmua, double* gmus, cudaStream_t st);
 cudaError_t launch_adj_restore(int* step, int c, unsigned* smax, const unsigned* saved,
                                cudaStream_t st);
+
+}  // namespace trinity
+
+namespace trinity {
+
+// Two-level angular grid launchers (defined in twolevel.cu).
+cudaError_t launch_sweep2(const GridParams& g, const DirInfo* dirs, const int8_t* offs, const int* children,
+                          int nch, int na_s, const float* Iring, const float* Sring, const float* mut,
+                          const float* nidx, float* Qf, float* Qc, RunState rs, cudaStream_t st);
+cudaError_t launch_refine(const GridParams& g, const DirInfo* dirs, const int* children, int nch, int na_s,
+                          const float* mut, const float* Qf, const float* Sring, float* Iring, RunState rs,
+                          cudaStream_t st);
+cudaError_t launch_recoarsen(int nvox, const int* vox, const int* children, int nch, int na_s, const float* Qf,
+                             float* Qc, int nv, cudaStream_t st);
 
 }  // namespace trinity

@@ -152,7 +152,7 @@ __device__ __forceinline__ float warp_transpose_max(float (&vals)[32], int lane)
 
 template <int NA>
 __global__ void __launch_bounds__(ScatterCfg<NA>::kThreads)
-    scatter_fp32_kernel(GridParams g, const DirInfo* __restrict__ dirs, const float* __restrict__ P,
+    scatter_fp32_kernel(GridParams g, const float* __restrict__ b1ds, int nch, const float* __restrict__ P,
                         const float* __restrict__ rcorr, const float* __restrict__ Q,
                         const float* __restrict__ mut, const float* __restrict__ eps,
                         const float* __restrict__ nidx,
@@ -193,7 +193,8 @@ __global__ void __launch_bounds__(ScatterCfg<NA>::kThreads)
   __syncthreads();
 
   float q[kTile], b1[kTile], so[kTile], acc[kTile];
-  const float ds = live ? dirs[i].ds : 0.0f;
+  const float* dsl = b1ds + static_cast<size_t>(live ? i : 0) * nch;
+  const float inv_nch = 1.0f / static_cast<float>(nch);
   const float ri = live ? rcorr[i] : 0.0f;
   const bool has_prev = (n - 1) >= g.hist_from;
   const size_t prev_off = (static_cast<size_t>(ring_slot(n - 1)) * g.na + (live ? i : 0)) * plane;
@@ -202,8 +203,16 @@ __global__ void __launch_bounds__(ScatterCfg<NA>::kThreads)
     const int vv = v0 + v;
     const bool ok = live && vv < g.nv;
     q[v] = ok ? __ldg(Q + static_cast<size_t>(i) * plane + vv) : 0.0f;
-    const float xo = ok ? mut[vv] * ds : 0.0f;
-    b1[v] = ok ? ray_b1(xo, expf(-xo)) : 0.0f;
+    // b1 of the direction, or the mean of its children's b1 on a two-level angular grid
+    float bs = 0.0f;
+    if (ok) {
+      const float mu = mut[vv];
+      for (int k = 0; k < nch; ++k) {
+        const float xo = mu * dsl[k];
+        bs += ray_b1(xo, expf(-xo));
+      }
+    }
+    b1[v] = bs * inv_nch;
     so[v] = (ok && has_prev) ? Sring[prev_off + vv] : 0.0f;
   }
   if (live) {
@@ -469,7 +478,7 @@ cudaError_t launch_sweep(const GridParams& g, const DirInfo* dirs, const int8_t*
   return cudaGetLastError();
 }
 
-cudaError_t launch_scatter_fp32(const GridParams& g, const DirInfo* dirs, const float* P,
+cudaError_t launch_scatter_fp32(const GridParams& g, const float* b1ds, int nch, const float* P,
                                 const float* rcorr, const float* Q, const float* mut,
                                 const float* eps, const float* nidx, float* Iring, float* Sring,
                                 float tol, int max_iters, RunState rs, cudaStream_t st) {
@@ -477,15 +486,15 @@ cudaError_t launch_scatter_fp32(const GridParams& g, const DirInfo* dirs, const 
   switch (g.na) {
     case 12:
       scatter_fp32_kernel<12><<<tiles, ScatterCfg<12>::kThreads, 0, st>>>(
-          g, dirs, P, rcorr, Q, mut, eps, nidx, Iring, Sring, tol, max_iters, rs);
+          g, b1ds, nch, P, rcorr, Q, mut, eps, nidx, Iring, Sring, tol, max_iters, rs);
       break;
     case 48:
       scatter_fp32_kernel<48><<<tiles, ScatterCfg<48>::kThreads, 0, st>>>(
-          g, dirs, P, rcorr, Q, mut, eps, nidx, Iring, Sring, tol, max_iters, rs);
+          g, b1ds, nch, P, rcorr, Q, mut, eps, nidx, Iring, Sring, tol, max_iters, rs);
       break;
     case 192:
       scatter_fp32_kernel<192><<<tiles, ScatterCfg<192>::kThreads, 0, st>>>(
-          g, dirs, P, rcorr, Q, mut, eps, nidx, Iring, Sring, tol, max_iters, rs);
+          g, b1ds, nch, P, rcorr, Q, mut, eps, nidx, Iring, Sring, tol, max_iters, rs);
       break;
     default:
       return cudaErrorInvalidValue;

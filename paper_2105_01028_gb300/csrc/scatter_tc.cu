@@ -277,7 +277,7 @@ __device__ __forceinline__ void load_b_operand(uint8_t* sB, const uint16_t* __re
 template <int NA>
 __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
     scatter_tc_kernel(GridParams g, const float* __restrict__ rcorr, const uint8_t* __restrict__ cls,
-                      const float* __restrict__ cls_ds, int ncls, const uint16_t* __restrict__ Pbf,
+                      const float* __restrict__ cls_ds, int ncls, int nch, const uint16_t* __restrict__ Pbf,
                       const float* __restrict__ Q, const float* __restrict__ mut, const float* __restrict__ eps,
                       const float* __restrict__ nidx, float* __restrict__ Iring, float* __restrict__ Sring,
                       float tol, int max_iters, RunState rs) {
@@ -371,11 +371,20 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
       e_s[tid] = ev;
       rho_s[tid] = rho;
     }
+    // a class is one spacing ds, or on a two-level angular grid the nch spacings of a
+    // coarse direction's children (b1 is then their mean)
     for (int u = tid; u < ncls * kM; u += blockDim.x) {
       const int k = u / kM, r = u % kM;
       const int vv = v0 + r;
-      const float x = vv < g.nv ? mut[vv] * cls_ds[k] : 0.0f;
-      b1t[k * kM + r] = vv < g.nv ? ray_b1(x, expf(-x)) : 0.0f;
+      float bs = 0.0f;
+      if (vv < g.nv) {
+        const float mu = mut[vv];
+        for (int j = 0; j < nch; ++j) {
+          const float x = mu * cls_ds[k * nch + j];
+          bs += ray_b1(x, expf(-x));
+        }
+      }
+      b1t[k * kM + r] = bs * (1.0f / static_cast<float>(nch));
     }
     __syncthreads();
 
@@ -708,10 +717,10 @@ cudaError_t launch_scatter_bf16(const GridParams& g, const BfTables& t, const ui
   const int ntiles = (g.nv + kM - 1) / kM;
   const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
   if (g.na == 48) {
-    scatter_tc_kernel<48><<<grid, Tc<48>::kThreads, Tc<48>::SMEM, st>>>(g, t.rcorr, t.cls, t.cls_ds, t.ncls, Pbf, Q, mut,
+    scatter_tc_kernel<48><<<grid, Tc<48>::kThreads, Tc<48>::SMEM, st>>>(g, t.rcorr, t.cls, t.cls_ds, t.ncls, t.nch, Pbf, Q, mut,
                                                                   eps, nidx, Iring, Sring, tol, max_iters, rs);
   } else if (g.na == 192) {
-    scatter_tc_kernel<192><<<grid, Tc<192>::kThreads, Tc<192>::SMEM, st>>>(g, t.rcorr, t.cls, t.cls_ds, t.ncls, Pbf, Q,
+    scatter_tc_kernel<192><<<grid, Tc<192>::kThreads, Tc<192>::SMEM, st>>>(g, t.rcorr, t.cls, t.cls_ds, t.ncls, t.nch, Pbf, Q,
                                                                     mut, eps, nidx, Iring, Sring, tol, max_iters, rs);
   } else {
     return cudaErrorInvalidValue;
