@@ -221,7 +221,8 @@ def workload_config(args):
                 args.spinup + args.warmup, args.spinup + args.warmup + args.steps - 1),
             "tol": 1e-6, "l2": "inputs larger than L2 (%s time-level history per solve)" % hist,
             "parallelism": "replicas" if dist_env()[0] > 1 else "single GPU",
-            "precision": args.precision}
+            "precision": args.precision,
+            "source_function": "exact per-voxel solve S = M Q" if args.exact else "source iteration (Eq. 12)"}
 
 
 def run_serve(args):
@@ -427,6 +428,8 @@ def main():
                     help="run the served stream with N requests instead of the slab")
     ap.add_argument("--rate", type=float, default=8.0, help="served stream arrival rate (1/s)")
     ap.add_argument("--slots", type=int, default=8, help="served stream concurrent slots")
+    ap.add_argument("--exact", action="store_true",
+                    help="exact per-voxel source function (one optics class on the slab) instead of the iteration")
     ap.add_argument("--two-level", action="store_true",
                     help="slab on the paper's fiducial angles: 3072 transport, 192 source-function dirs")
     ap.add_argument("--adjoint", action="store_true", help="gradient workload (checkpointed adjoint)")
@@ -459,6 +462,8 @@ def main():
         prob["nside_scatter"] = 4
     else:
         prob = W.config_slab(steps=total, precision=args.precision, nx=nx, ny=ny, nz=nz)
+    if args.exact:
+        prob["exact"] = True
     stream = torch.cuda.Stream()
     nv = prob["nx"] * prob["ny"] * prob["nz"]
     na = 12 * prob["nside"] ** 2          # transport directions (updates are counted on these)
@@ -523,7 +528,7 @@ def main():
     per = [kms[0] / kp, kms[1] / kp, kms[2] / kp]
     tot = sum(per)
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    if args.precision == "bf16":
+    if args.precision == "bf16" and not args.exact:
         s_bound, s_peak, s_unit = "tensor", pk.get("bf16_tflops_sustained", 1700.0), "TFLOP/s"
     else:
         s_bound, s_peak, s_unit = "alu", fp32_peak, "TFLOP/s"
@@ -534,7 +539,7 @@ def main():
          "achieved": w_ach, "peak": hbm, "unit": "GB/s", "frac": w_ach / hbm,
          "algorithmic_bytes": sweep_bytes,
          "traffic": measured_traffic("sweep2_kernel" if nch > 1 else "sweep_kernel", nv * na)},
-        {"name": "scatter_" + args.precision, "ms": per[1], "share": per[1] / tot,
+        {"name": "exact_fp32" if args.exact else "scatter_" + args.precision, "ms": per[1], "share": per[1] / tot,
          "bound": s_bound, "achieved": s_ach, "peak": s_peak, "unit": s_unit,
          "frac": s_ach / s_peak, "algorithmic_flops": scat_flops,
          "hbm_gbs": scat_bytes / (per[1] * 1e-3) / 1e9},
@@ -558,7 +563,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16-scatter/f32-sweep" if args.precision == "bf16" else "f32",
+            "dtype": "f32" if (args.exact or args.precision == "fp32") else "bf16-scatter/f32-sweep",
             "data": "synthetic", "config": workload_config(args),
             "gpu_launches": (5 if nch > 1 else 4) * args.steps,
             "iterations": {"mean": float(np.mean(win_mean)), "max": int(np.max(win_max))},
@@ -585,10 +590,10 @@ def main():
         line["fp32"] = {"value": ws * updates / (m32 * 1e-3), "ms_per_step": m32 / args.steps}
         f32.close()
 
-    if args.two_level:
+    if args.two_level or args.exact:
         line["cpu_baseline"] = None
-        line["cpu_baseline_note"] = "the timed oracle leg samples the one-level step only"
-    if rank == 0 and not args.no_cpu and ws >= 1 and not args.two_level:
+        line["cpu_baseline_note"] = "the timed oracle leg samples the one-level iterated step only"
+    if rank == 0 and not args.no_cpu and ws >= 1 and not (args.two_level or args.exact):
         v, info = CpuLeg(prob).sample(args.cpu_voxels, seed=100)
         line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": cpu_cores(),
                                 "kind": "oracle",

@@ -122,6 +122,20 @@ int trinity_set_optics_uniform(trinity_ctx* ctx, double mua, double mus, double 
  * rebuilt from the n map of each trinity_set_optics call.  Before the first step. */
 int trinity_set_fresnel(trinity_ctx* ctx, int on);
 
+/* Exact per-voxel source function instead of the source iteration, for piecewise-uniform
+ * optics.  The iteration of Eq. 12 (Section 2.4 steps 5-6) converges to the fixed point
+ * of S = a P (Q + b1 S); voxels with the same (mu_t, mu_a/mu_t) share the operator
+ * M = (I - a P B1)^-1 a P (B1 = diag b1(mu_t ds_d)), so with ``on`` set each step takes
+ * S = M Q in one product per voxel.  The operators are built on the host in FP64 (from
+ * the FP32 phase matrix with its diagonal correction, the matrix the iteration applies)
+ * at this call and at every trinity_set_optics, and applied in FP32 in either precision
+ * mode.  TRINITY_E_UNSUPPORTED if the optics have more than 8 distinct pairs (the mode
+ * is then off) or on a two-level angular grid.  Before the first step. */
+int trinity_set_exact_solve(trinity_ctx* ctx, int on);
+
+/* Number of optics classes the exact solve uses (0 when it is off). */
+int trinity_exact_classes(const trinity_ctx* ctx, int* n);
+
 /* Number of interface voxels in the context's current table. */
 int trinity_interface_count(const trinity_ctx* ctx, int* n);
 

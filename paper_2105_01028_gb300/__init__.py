@@ -82,6 +82,8 @@ class Forward:
         self._check(self.set_optics(prob["mua"], prob["mus"], prob["nidx"], prob["g"]))
         if prob.get("fresnel", False):
             self._check(self.L.trinity_set_fresnel(self.h, 1))
+        if prob.get("exact", False):
+            self._check(self.L.trinity_set_exact_solve(self.h, 1))
         src = prob.get("source")
         if src is not None:
             self._check(self.L.trinity_set_source(self.h, int(src["face"]), float(src["u_mm"]),
@@ -122,6 +124,12 @@ class Forward:
         if not (ka == ks == kn):
             raise ValueError("optics maps must all be host arrays or all device tensors")
         return self.L.trinity_set_optics(self.h, pa, ps, pn, float(g), ka)
+
+    def exact_classes(self):
+        """Optics classes of the exact solve (0 when it is off)."""
+        n = ctypes.c_int()
+        self._check(self.L.trinity_exact_classes(self.h, ctypes.byref(n)))
+        return n.value
 
     def interface_count(self):
         n = ctypes.c_int()

@@ -86,6 +86,13 @@ struct trinity_ctx {
   float* Qc = nullptr;       // [na_s][N_v] mean Q over each coarse bin's children
   float* Ic = nullptr;       // [5][na_s][N_v] coarse mean intensity (written by the scatter)
 
+  // exact per-voxel source function for piecewise-uniform optics
+  bool exact = false;
+  int n_xcls = 0;
+  float* d_Mt = nullptr;       // [classes][na][na] operators M = (I - a P B1)^-1 a P, transposed
+  uint8_t* d_xcls = nullptr;   // [nv] optics class of each voxel
+  std::vector<float> h_P32, h_rc32, h_mut, h_eps;  // host copies the operators are built from
+
   // index interfaces (Eqs. 13-14)
   bool fresnel = false;
   std::vector<float> nmap;  // host copy of the refractive-index map
@@ -474,7 +481,10 @@ int enqueue_transport(trinity_ctx* ctx, const RunState& rs) {
 // The per-voxel source iteration (Eq. 12) on the source function's directions.
 int enqueue_scatter(trinity_ctx* ctx, const RunState& rs) {
   const GridParams& gs = ctx->g_s;
-  if (ctx->desc.precision == TRINITY_BF16) {
+  if (ctx->exact) {
+    CK(launch_exact_fp32(gs, ctx->d_b1ds, ctx->nch, ctx->d_Mt, ctx->d_xcls, ctx->Qc, ctx->mut, ctx->nidx,
+                         ctx->Ic, ctx->S, rs, ctx->stream));
+  } else if (ctx->desc.precision == TRINITY_BF16) {
     CK(launch_scatter_bf16(gs, bf_tables(ctx), ctx->Pbf, ctx->Qc, ctx->mut, ctx->eps, ctx->nidx, ctx->Ic,
                            ctx->S, static_cast<float>(ctx->desc.tol), ctx->desc.max_iters, rs,
                            ctx->stream));
@@ -522,6 +532,74 @@ uint16_t to_bf16(float f) {
   const uint32_t lsb = (u >> 16) & 1u;
   u += 0x7fffu + lsb;  // round to nearest even (inputs are finite)
   return static_cast<uint16_t>(u >> 16);
+}
+
+constexpr int kMaxExactClasses = 8;
+
+// Optics classes and their exact operators M = (I - a P~ B1)^-1 a P~ (FP64 solve; P~ is
+// the FP32 phase matrix plus its diagonal correction, the matrix the iteration applies).
+int build_exact(trinity_ctx* ctx) {
+  if (!ctx->exact || !ctx->optics_set) return TRINITY_OK;
+  if (ctx->two_level)
+    return fail(ctx, TRINITY_E_UNSUPPORTED, "the exact solve covers one angular grid (nside_scatter = nside)");
+  const int na = ctx->g.na;
+  const size_t nv = ctx->g.nv;
+  std::vector<std::pair<uint64_t, int>> keys;
+  std::vector<uint8_t> cls(nv);
+  std::vector<std::pair<float, float>> pairs;
+  for (size_t v = 0; v < nv; ++v) {
+    uint32_t a, b;
+    std::memcpy(&a, &ctx->h_mut[v], 4);
+    std::memcpy(&b, &ctx->h_eps[v], 4);
+    const uint64_t key = (static_cast<uint64_t>(a) << 32) | b;
+    size_t k = 0;
+    while (k < keys.size() && keys[k].first != key) ++k;
+    if (k == keys.size()) {
+      if (keys.size() == kMaxExactClasses)
+        return fail(ctx, TRINITY_E_UNSUPPORTED,
+                    "the exact solve needs piecewise-uniform optics: more than 8 distinct (mu_t, mu_a/mu_t) pairs");
+      keys.push_back({key, static_cast<int>(k)});
+      pairs.push_back({ctx->h_mut[v], ctx->h_eps[v]});
+    }
+    cls[v] = static_cast<uint8_t>(k);
+  }
+  std::vector<double> Pt(static_cast<size_t>(na) * na);
+  for (int i = 0; i < na; ++i)
+    for (int j = 0; j < na; ++j)
+      Pt[static_cast<size_t>(i) * na + j] =
+          static_cast<double>(ctx->h_P32[static_cast<size_t>(i) * na + j]) + (i == j ? double(ctx->h_rc32[i]) : 0.0);
+  std::vector<float> Mt(pairs.size() * static_cast<size_t>(na) * na);
+  for (size_t c = 0; c < pairs.size(); ++c) {
+    const double mt = pairs[c].first, a = 1.0 - static_cast<double>(pairs[c].second);
+    std::vector<double> A(static_cast<size_t>(na) * na), B(static_cast<size_t>(na) * na);
+    std::vector<double> b1(na);
+    for (int d = 0; d < na; ++d) b1[d] = ray_b1_fp64(mt * static_cast<double>(static_cast<float>(ctx->lat.ds[d])));
+    for (int i = 0; i < na; ++i)
+      for (int j = 0; j < na; ++j) {
+        const double p = Pt[static_cast<size_t>(i) * na + j];
+        A[static_cast<size_t>(i) * na + j] = (i == j ? 1.0 : 0.0) - a * p * b1[j];
+        B[static_cast<size_t>(i) * na + j] = a * p;
+      }
+    std::vector<double> M;
+    try {
+      M = solve_dense(A, B, na);
+    } catch (const std::exception& e) {
+      return fail(ctx, TRINITY_E_INVALID, e.what());
+    }
+    for (int i = 0; i < na; ++i)
+      for (int j = 0; j < na; ++j)
+        Mt[(c * na + j) * static_cast<size_t>(na) + i] = static_cast<float>(M[static_cast<size_t>(i) * na + j]);
+  }
+  cudaFree(ctx->d_Mt);
+  cudaFree(ctx->d_xcls);
+  ctx->d_Mt = nullptr;
+  ctx->d_xcls = nullptr;
+  CK(dalloc(&ctx->d_Mt, Mt.size()));
+  CK(dalloc(&ctx->d_xcls, nv));
+  CK(cudaMemcpy(ctx->d_Mt, Mt.data(), Mt.size() * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_xcls, cls.data(), nv, cudaMemcpyHostToDevice));
+  ctx->n_xcls = static_cast<int>(pairs.size());
+  return TRINITY_OK;
 }
 
 }  // namespace
@@ -773,6 +851,14 @@ int trinity_set_optics(trinity_ctx* ctx, const float* mua, const float* mus, con
   ctx->g_aniso = g;
   ctx->optics_set = true;
   ctx->nmap = r;
+  ctx->h_P32 = P32;
+  ctx->h_rc32 = rc;
+  ctx->h_mut = mt;
+  ctx->h_eps = al;
+  {
+    const int rc3 = build_exact(ctx);
+    if (rc3 != TRINITY_OK) return rc3;
+  }
   {
     const int rc2 = build_interface_table(ctx);
     if (rc2 != TRINITY_OK) return rc2;
@@ -793,6 +879,21 @@ int trinity_set_fresnel(trinity_ctx* ctx, int on) {
   if (ctx->locked) return fail(ctx, TRINITY_E_STATE, "interfaces must be set before the first step");
   ctx->fresnel = on != 0;
   return build_interface_table(ctx);
+}
+
+int trinity_set_exact_solve(trinity_ctx* ctx, int on) {
+  if (!ctx) return TRINITY_E_INVALID;
+  if (ctx->locked) return fail(ctx, TRINITY_E_STATE, "the exact solve must be chosen before the first step");
+  ctx->exact = on != 0;
+  const int rc = build_exact(ctx);
+  if (rc != TRINITY_OK) ctx->exact = false;
+  return rc;
+}
+
+int trinity_exact_classes(const trinity_ctx* ctx, int* n) {
+  if (!ctx || !n) return TRINITY_E_INVALID;
+  *n = ctx->exact ? ctx->n_xcls : 0;
+  return TRINITY_OK;
 }
 
 int trinity_interface_count(const trinity_ctx* ctx, int* n) {
@@ -1397,6 +1498,8 @@ void trinity_destroy(trinity_ctx* ctx) {
   }
   cudaFree(ctx->d_children);
   cudaFree(ctx->d_b1ds);
+  cudaFree(ctx->d_Mt);
+  cudaFree(ctx->d_xcls);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   void* bufs[] = {ctx->I,         ctx->S,          ctx->Q,           ctx->mut,       ctx->eps,
                   ctx->nidx,      ctx->P32,        ctx->Pbf,         ctx->d_dirs,    ctx->d_offs,

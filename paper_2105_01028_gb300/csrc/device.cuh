@@ -179,3 +179,13 @@ cudaError_t launch_recoarsen(int nvox, const int* vox, const int* children, int 
                              float* Qc, int nv, cudaStream_t st);
 
 }  // namespace trinity
+
+namespace trinity {
+
+// Exact per-voxel source function for piecewise-uniform optics (defined in exact.cu).
+// Mt: [classes][na][na] FP32, M transposed; cls: [nv] class of each voxel (< 32).
+cudaError_t launch_exact_fp32(const GridParams& g, const float* b1ds, int nch, const float* Mt,
+                              const uint8_t* cls, const float* Q, const float* mut, const float* nidx,
+                              float* Iring, float* Sring, RunState rs, cudaStream_t st);
+
+}  // namespace trinity

@@ -450,3 +450,49 @@ InterfaceTable build_interfaces(const std::vector<double>& dirs, const Lattice& 
 }
 
 }  // namespace trinity
+
+namespace trinity {
+
+std::vector<double> solve_dense(std::vector<double> A, std::vector<double> B, int n) {
+  // Gaussian elimination with partial pivoting on [A | B], B with n columns
+  for (int k = 0; k < n; ++k) {
+    int piv = k;
+    double best = std::fabs(A[static_cast<size_t>(k) * n + k]);
+    for (int r = k + 1; r < n; ++r) {
+      const double a = std::fabs(A[static_cast<size_t>(r) * n + k]);
+      if (a > best) {
+        best = a;
+        piv = r;
+      }
+    }
+    if (!(best > 0.0)) throw std::runtime_error("singular system");
+    if (piv != k)
+      for (int c = 0; c < n; ++c) {
+        std::swap(A[static_cast<size_t>(k) * n + c], A[static_cast<size_t>(piv) * n + c]);
+        std::swap(B[static_cast<size_t>(k) * n + c], B[static_cast<size_t>(piv) * n + c]);
+      }
+    const double inv = 1.0 / A[static_cast<size_t>(k) * n + k];
+    for (int r = k + 1; r < n; ++r) {
+      const double f = A[static_cast<size_t>(r) * n + k] * inv;
+      if (f == 0.0) continue;
+      for (int c = k; c < n; ++c) A[static_cast<size_t>(r) * n + c] -= f * A[static_cast<size_t>(k) * n + c];
+      for (int c = 0; c < n; ++c) B[static_cast<size_t>(r) * n + c] -= f * B[static_cast<size_t>(k) * n + c];
+    }
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const double inv = 1.0 / A[static_cast<size_t>(k) * n + k];
+    for (int c = 0; c < n; ++c) {
+      double acc = B[static_cast<size_t>(k) * n + c];
+      for (int j = k + 1; j < n; ++j) acc -= A[static_cast<size_t>(k) * n + j] * B[static_cast<size_t>(j) * n + c];
+      B[static_cast<size_t>(k) * n + c] = acc * inv;
+    }
+  }
+  return B;
+}
+
+double ray_b1_fp64(double x) {
+  if (x < 1e-3) return x / 2 - x * x / 6 + x * x * x / 24 - x * x * x * x / 120;
+  return (x - 1.0 + std::exp(-x)) / x;
+}
+
+}  // namespace trinity

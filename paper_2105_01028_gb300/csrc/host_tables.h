@@ -20,6 +20,12 @@ long ring_pixel(int nside, double z, double phi);
 // Coarse pixel containing each fine pixel's centre (its parent in the nested hierarchy).
 std::vector<int> parent_map(int nside_fine, int nside_coarse);
 
+// X solving A X = B for dense n x n A and B (row-major, partial pivoting); throws if singular.
+std::vector<double> solve_dense(std::vector<double> A, std::vector<double> B, int n);
+
+// b1(x) of Eq. 9 in FP64 (Taylor series below x = 1e-3).
+double ray_b1_fp64(double x);
+
 // Normalised phase matrix of Eq. 12 (row-major N_a x N_a) and its g_eff.
 std::vector<double> phase_matrix(int nside, double g, double* g_eff);
 

@@ -1,0 +1,87 @@
+"""Exact per-voxel source function (trinity_set_exact_solve) on the GPU against the
+oracle's ExactSolver, which is pinned to the fixed-point equation and to the converged
+iteration on the CPU (test_oracle_exact.py).
+
+Bars are the FP32 iteration's (test_gpu_parity.py): detector curves and energy 2e-5 of
+their peak, whole fields 2e-4 of their peak.  The exact path replaces the iteration's
+stopping error by one FP32 product with an operator that the host builds in FP64.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.exact import ExactSolver
+from test_oracle_exact import phantom
+
+pytestmark = pytest.mark.gpu
+
+DET_TOL = 2e-5
+FIELD_TOL = 2e-4
+
+
+def _lib():
+    import paper_2105_01028_gb300 as P
+    return P
+
+
+def _run(p, steps):
+    P = _lib()
+    fw = P.Forward(p)
+    fw.step(steps)
+    out = dict(det=fw.detectors(), N=fw.energy()[0], I=fw.field(P.FIELD_I), S=fw.field(P.FIELD_S),
+               classes=fw.exact_classes())
+    fw.close()
+    return out
+
+
+@pytest.mark.parametrize("nside", [2, 4])
+def test_exact_matches_oracle(nside):
+    steps = 12 if nside == 2 else 8
+    p = phantom(nside=nside, steps=steps, tol=1e-6)
+    p["exact"] = True
+    s = ExactSolver(dict(p, mua=np.asarray(p["mua"], np.float64), mus=np.asarray(p["mus"], np.float64)))
+    ref = s.run(steps)
+    g = _run(p, steps)
+    assert g["classes"] == 3
+    assert np.max(np.abs(g["det"] - ref["detectors"])) <= DET_TOL * np.max(np.abs(ref["detectors"]))
+    assert np.max(np.abs(g["N"] - ref["energy"])) <= DET_TOL * np.max(ref["energy"])
+    I_ref, S_ref = s.level("I"), s.level("S")
+    assert np.max(np.abs(g["I"] - I_ref)) <= FIELD_TOL * np.max(np.abs(I_ref))
+    assert np.max(np.abs(g["S"] - S_ref)) <= FIELD_TOL * np.max(np.abs(S_ref))
+
+
+def test_exact_agrees_with_the_converged_gpu_iteration():
+    p = phantom(nside=2, steps=16, tol=1e-8)
+    it = _run(dict(p), 16)
+    ex = _run(dict(p, exact=True), 16)
+    assert it["classes"] == 0 and ex["classes"] == 3
+    assert np.max(np.abs(it["det"] - ex["det"])) <= DET_TOL * np.max(np.abs(ex["det"]))
+    assert np.max(np.abs(it["I"] - ex["I"])) <= FIELD_TOL * np.max(np.abs(ex["I"]))
+
+
+def test_bf16_context_takes_the_same_exact_path():
+    p = phantom(nside=4, steps=6, tol=1e-6)
+    a = _run(dict(p, exact=True, precision="fp32"), 6)
+    b = _run(dict(p, exact=True, precision="bf16"), 6)
+    assert np.array_equal(a["I"], b["I"]) and np.array_equal(a["S"], b["S"])
+
+
+def test_homogeneous_slab_is_one_class():
+    p = W.config_slab(steps=8, nx=24, ny=24, nz=16)
+    p["exact"] = True
+    g = _run(p, 8)
+    assert g["classes"] == 1 and np.max(g["det"]) > 0
+
+
+def test_exact_rejects_continuous_optics_and_two_level_grids():
+    P = _lib()
+    p, _ = W.config_adjoint(n=8, nside=2, steps=4)  # log-normal random field: 512 classes
+    with pytest.raises(P.TrinityError, match="E_UNSUPPORTED"):
+        P.Forward(dict(p, exact=True))
+    fw = P.Forward(p)
+    assert fw.L.trinity_set_exact_solve(fw.h, 1) != 0 and fw.exact_classes() == 0
+    fw.step(2)  # still steps with the iteration
+    q = W.homogeneous(6, 6, 6, 4, 0.02, 2.0, steps=4)
+    q["nside_scatter"] = 2
+    with pytest.raises(P.TrinityError, match="E_UNSUPPORTED"):
+        P.Forward(dict(q, exact=True))
