@@ -76,6 +76,24 @@ def measured_traffic(kernel, updates):
     return None
 
 
+def max_over_ranks(ms):
+    """The slowest rank's time (ms) when the bench runs as several ranks (one replica per
+    GPU under torch.distributed), else ``ms`` itself."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ws, updates_per_rank, ms):
+    """Whole-job throughput: the updates of all ``ws`` replicas over the slowest rank's time."""
+    return ws * updates_per_rank / (ms * 1e-3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -492,10 +510,7 @@ def main():
         stream.synchronize()
     ms = ev0.elapsed_time(ev1)
     torch.cuda.synchronize()
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms)
     status = fwd.sync()
     det = fwd.detectors()
     N, esc = fwd.energy()
@@ -513,7 +528,7 @@ def main():
     fwd.close()
 
     updates = nv * na * args.steps
-    value = ws * updates / (ms * 1e-3)
+    value = job_value(ws, updates, ms)
     pk = peaks()
     hbm = pk["hbm_gbs"]
     if nch == 1:
