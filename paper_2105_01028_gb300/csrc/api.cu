@@ -90,6 +90,7 @@ struct trinity_ctx {
   bool exact = false;
   int n_xcls = 0;
   float* d_Mt = nullptr;       // [classes][na][na] operators M = (I - a P B1)^-1 a P, transposed
+  float* d_b1tab = nullptr;    // [classes][na] b1 of each class and direction
   uint8_t* d_xcls = nullptr;   // [nv] optics class of each voxel
   std::vector<float> h_P32, h_rc32, h_mut, h_eps;  // host copies the operators are built from
 
@@ -482,8 +483,8 @@ int enqueue_transport(trinity_ctx* ctx, const RunState& rs) {
 int enqueue_scatter(trinity_ctx* ctx, const RunState& rs) {
   const GridParams& gs = ctx->g_s;
   if (ctx->exact) {
-    CK(launch_exact_fp32(gs, ctx->d_b1ds, ctx->nch, ctx->d_Mt, ctx->d_xcls, ctx->Qc, ctx->mut, ctx->nidx,
-                         ctx->Ic, ctx->S, rs, ctx->stream));
+    CK(launch_exact_fp32(gs, ctx->d_b1ds, ctx->nch, ctx->d_Mt, ctx->d_b1tab, ctx->d_xcls, ctx->Qc, ctx->mut,
+                         ctx->nidx, ctx->Ic, ctx->S, rs, ctx->stream));
   } else if (ctx->desc.precision == TRINITY_BF16) {
     CK(launch_scatter_bf16(gs, bf_tables(ctx), ctx->Pbf, ctx->Qc, ctx->mut, ctx->eps, ctx->nidx, ctx->Ic,
                            ctx->S, static_cast<float>(ctx->desc.tol), ctx->desc.max_iters, rs,
@@ -569,11 +570,15 @@ int build_exact(trinity_ctx* ctx) {
       Pt[static_cast<size_t>(i) * na + j] =
           static_cast<double>(ctx->h_P32[static_cast<size_t>(i) * na + j]) + (i == j ? double(ctx->h_rc32[i]) : 0.0);
   std::vector<float> Mt(pairs.size() * static_cast<size_t>(na) * na);
+  std::vector<float> b1tab(pairs.size() * static_cast<size_t>(na));
   for (size_t c = 0; c < pairs.size(); ++c) {
     const double mt = pairs[c].first, a = 1.0 - static_cast<double>(pairs[c].second);
     std::vector<double> A(static_cast<size_t>(na) * na), B(static_cast<size_t>(na) * na);
     std::vector<double> b1(na);
-    for (int d = 0; d < na; ++d) b1[d] = ray_b1_fp64(mt * static_cast<double>(static_cast<float>(ctx->lat.ds[d])));
+    for (int d = 0; d < na; ++d) {
+      b1[d] = ray_b1_fp64(mt * static_cast<double>(static_cast<float>(ctx->lat.ds[d])));
+      b1tab[c * na + d] = static_cast<float>(b1[d]);
+    }
     for (int i = 0; i < na; ++i)
       for (int j = 0; j < na; ++j) {
         const double p = Pt[static_cast<size_t>(i) * na + j];
@@ -592,11 +597,16 @@ int build_exact(trinity_ctx* ctx) {
   }
   cudaFree(ctx->d_Mt);
   cudaFree(ctx->d_xcls);
+  cudaFree(ctx->d_b1tab);
+  cudaFree(ctx->d_b1tab);
   ctx->d_Mt = nullptr;
   ctx->d_xcls = nullptr;
+  ctx->d_b1tab = nullptr;
   CK(dalloc(&ctx->d_Mt, Mt.size()));
   CK(dalloc(&ctx->d_xcls, nv));
+  CK(dalloc(&ctx->d_b1tab, b1tab.size()));
   CK(cudaMemcpy(ctx->d_Mt, Mt.data(), Mt.size() * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_b1tab, b1tab.data(), b1tab.size() * 4, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_xcls, cls.data(), nv, cudaMemcpyHostToDevice));
   ctx->n_xcls = static_cast<int>(pairs.size());
   return TRINITY_OK;

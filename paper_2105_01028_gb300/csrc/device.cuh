@@ -184,8 +184,9 @@ namespace trinity {
 
 // Exact per-voxel source function for piecewise-uniform optics (defined in exact.cu).
 // Mt: [classes][na][na] FP32, M transposed; cls: [nv] class of each voxel (< 32).
+// b1tab: [classes][na] b1 of each class and direction (the 192-direction GEMM form uses it).
 cudaError_t launch_exact_fp32(const GridParams& g, const float* b1ds, int nch, const float* Mt,
-                              const uint8_t* cls, const float* Q, const float* mut, const float* nidx,
-                              float* Iring, float* Sring, RunState rs, cudaStream_t st);
+                              const float* b1tab, const uint8_t* cls, const float* Q, const float* mut,
+                              const float* nidx, float* Iring, float* Sring, RunState rs, cudaStream_t st);
 
 }  // namespace trinity

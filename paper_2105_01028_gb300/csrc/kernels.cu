@@ -25,6 +25,8 @@ __device__ __forceinline__ int pick(int axis, int x, int y, int z) {
 // threadIdx.y one row each), so a warp reads contiguous, at most one-voxel-shifted runs
 // of the upwind plane.  The direction's constants are staged in shared memory once per
 // block, and the lattice offsets are uniform along a row unless x is the dominant axis.
+// The block also resolves, once, where the five stored levels n - m (m = 0..4) of this
+// direction's plane live, so a voxel indexes them by its delay's whole part m.
 // ----------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) sweep_kernel(GridParams g, const DirInfo* __restrict__ dirs,
                                                     const int8_t* __restrict__ offs,
@@ -35,14 +37,24 @@ __global__ void __launch_bounds__(256) sweep_kernel(GridParams g, const DirInfo*
                                                     float* __restrict__ Q, RunState rs) {
   __shared__ DirInfo di_s;
   __shared__ int n_s;
+  __shared__ const float* ilev_s[5];  // plane d of I at level n - m, null before the history
+  __shared__ const float* slev_s[5];
   const int d = blockIdx.y;
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if (tid == 0) {
     di_s = dirs[d];
     n_s = *rs.step;
     if (d == 0 && blockIdx.x == 0) {
       rs.smax[n_s & 1] = 0u;     // max |S(n)|, filled by this step's source iteration
       rs.tile_ctr[n_s & 1] = 0;  // work counter of this step's persistent kernel
     }
+  }
+  __syncthreads();
+  if (tid < 5) {
+    const int L = n_s - tid;
+    const size_t o = (static_cast<size_t>(ring_slot(L)) * g.na + d) * static_cast<size_t>(g.nv);
+    ilev_s[tid] = L >= g.hist_from ? Iring + o : nullptr;
+    slev_s[tid] = L >= g.hist_from ? Sring + o : nullptr;
   }
   __syncthreads();
   const int row = blockIdx.x * blockDim.y + threadIdx.y;  // (y, z) row index
@@ -85,21 +97,21 @@ __global__ void __launch_bounds__(256) sweep_kernel(GridParams g, const DirInfo*
     int m;
     float f;
     retarded_delay(dc_hi, dc_lo, __ldg(nidx + v), m, f);
+    m = m < 1 ? 1 : (m > 3 ? 3 : m);  // the optics check keeps every delay in [1, 4)
     const int L0 = n - m, L1 = n - m - 1;
     float Iup = 0.0f, Sup = 0.0f;
     if (kind == 0) {
-      const size_t u = static_cast<size_t>(qd) * sd + static_cast<size_t>(q0) * s0 +
-                       static_cast<size_t>(q1) * s1;
+      const int u = qd * sd + q0 * s0 + q1 * s1;  // < nv <= 2^30
+      const float* i0p = ilev_s[m];
+      const float* i1p = ilev_s[m + 1];
       float i0 = 0.0f, i1 = 0.0f, s0v = 0.0f, s1v = 0.0f;
-      if (L0 >= g.hist_from) {
-        const size_t o = static_cast<size_t>(ring_slot(L0)) * g.na * plane + lev0 + u;
-        i0 = __ldg(Iring + o);
-        s0v = __ldg(Sring + o);
+      if (i0p) {
+        i0 = __ldg(i0p + u);
+        s0v = __ldg(slev_s[m] + u);
       }
-      if (L1 >= g.hist_from) {
-        const size_t o = static_cast<size_t>(ring_slot(L1)) * g.na * plane + lev0 + u;
-        i1 = __ldg(Iring + o);
-        s1v = __ldg(Sring + o);
+      if (i1p) {
+        i1 = __ldg(i1p + u);
+        s1v = __ldg(slev_s[m + 1] + u);
       }
       Iup = (1.0f - f) * i0 + f * i1;
       Sup = (1.0f - f) * s0v + f * s1v;
