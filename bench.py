@@ -567,9 +567,10 @@ def main():
                       "achieved": f_ach, "peak": hbm, "unit": "GB/s", "frac": f_ach / hbm,
                       "algorithmic_bytes": fin_bytes}
     dom = max(kernels[:2], key=lambda k: k["ms"])
-    traffic = (measured_traffic("scatter_tc_kernel", nv * na_s) if dom["name"] == "scatter_bf16"
-               else measured_traffic("sweep2_kernel" if nch > 1 else "sweep_kernel", nv * na)
-               if dom is kernels[0] else None)
+    scat_kernel = ("exact_gemm192_kernel" if args.exact else
+                   "scatter_tc_kernel" if args.precision == "bf16" else "scatter_fp32_kernel")
+    traffic = (measured_traffic(scat_kernel, nv * na_s) if dom is kernels[1]
+               else measured_traffic("sweep2_kernel" if nch > 1 else "sweep_kernel", nv * na))
     roof = {"kernel": dom["name"], "bound": dom["bound"], "achieved": dom["achieved"],
             "peak": dom["peak"], "unit": dom["unit"], "frac": dom["frac"], "traffic": traffic,
             "peak_source": pk["_source"] + (" (FP32 FFMA: 152 SMs x 128 lanes x 2 x max SM clock)"
