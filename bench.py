@@ -525,6 +525,7 @@ def main():
     kms = fwd.profile(kp)
     k_it_max, k_it_mean = fwd.iterations()
     k_mean = float(np.mean(k_it_mean[-kp:]))
+    executed = fwd.executed_iterations()[first:first + args.steps]
     fwd.close()
 
     updates = nv * na * args.steps
@@ -582,7 +583,8 @@ def main():
             "dtype": "f32" if (args.exact or args.precision == "fp32") else "bf16-scatter/f32-sweep",
             "data": "synthetic", "config": workload_config(args),
             "gpu_launches": (5 if nch > 1 else 4) * args.steps,
-            "iterations": {"mean": float(np.mean(win_mean)), "max": int(np.max(win_max))},
+            "iterations": {"mean": float(np.mean(win_mean)), "max": int(np.max(win_max)),
+                           "executed_per_voxel": float(np.mean(executed))},
             "status": int(status),
             "roofline": roof, "kernels": kernels, "clocks": clk.summary(),
             "e2e": {"value": ws * nv * na * job_steps / t_job, "unit": "updates/s",

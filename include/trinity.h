@@ -194,6 +194,12 @@ int trinity_read_energy(trinity_ctx* ctx, double* N_t, double* escaped, size_t n
 /* Per-step iteration statistics of the last ``nsteps`` steps: max and mean per voxel. */
 int trinity_read_iterations(trinity_ctx* ctx, int* iters_max, double* iters_mean, size_t nsteps);
 
+/* Iterations the BF16 tensor-core kernel executed per voxel in each of the last
+ * ``nsteps`` steps: a 128-voxel tile iterates until its slowest voxel stops, so this mean
+ * is at least the per-voxel mean of trinity_read_iterations; their ratio is the tile's
+ * idle work.  Zero in the other modes (they do not count it). */
+int trinity_read_executed_iterations(trinity_ctx* ctx, double* executed_mean, size_t nsteps);
+
 /* Copy a field (TRINITY_FIELD_I or _S) at time level (steps_done - 1 - back),
  * 0 <= back <= 4, into ``out`` ([N_a][nz*ny*nx] float32, ``bytes`` = its size). */
 int trinity_read_field(trinity_ctx* ctx, int what, int back, void* out, size_t bytes, int ptr_kind);

@@ -246,6 +246,14 @@ class Forward:
                                                    mean.ctypes.data_as(_lib.P_double), nsteps))
         return mx, mean
 
+    def executed_iterations(self, nsteps=None):
+        """Per step, the iterations the tensor-core kernel executed per voxel (its tiles run
+        until their slowest voxel stops); zeros in the other modes."""
+        nsteps = self.steps_done() if nsteps is None else nsteps
+        out = np.zeros(nsteps)
+        self._check(self.L.trinity_read_executed_iterations(self.h, out.ctypes.data_as(_lib.P_double), nsteps))
+        return out
+
     def field(self, what=FIELD_I, back=0, out=None):
         """Field at level steps_done-1-back as a host array [N_a, N_v] (or into a CUDA tensor);
         S has the source function's N_a (coarser on a two-level angular grid)."""

@@ -66,6 +66,7 @@ struct trinity_ctx {
   int ncls = 0;
   int* d_iters_max = nullptr;
   unsigned long long* d_iters_sum = nullptr;
+  unsigned long long* d_tile_iters = nullptr;
   double* d_energy = nullptr;
   double* d_escaped = nullptr;
   int* d_bins = nullptr;
@@ -214,6 +215,7 @@ RunState run_state(trinity_ctx* c) {
   rs.smax = c->d_smax;
   rs.iters_max = c->d_iters_max;
   rs.iters_sum = c->d_iters_sum;
+  rs.tile_iters = c->d_tile_iters;
   rs.energy = c->d_energy;
   rs.escaped = c->d_escaped;
   rs.nonconv = c->d_nonconv;
@@ -229,12 +231,14 @@ int ensure_capacity(trinity_ctx* ctx, int need) {
   int cap = std::max(256, ctx->capacity);
   while (cap < need) cap *= 2;
   int* im = nullptr;
-  unsigned long long* is = nullptr;
+  unsigned long long *is = nullptr, *ti = nullptr;
   double *en = nullptr, *es = nullptr;
   int* bins = nullptr;
   CK(cudaStreamSynchronize(ctx->stream));
   CK(dalloc(&im, cap));
   CK(dalloc(&is, cap));
+  CK(dalloc(&ti, cap));
+  CK(cudaMemset(ti, 0, cap * sizeof(unsigned long long)));
   CK(dalloc(&en, cap));
   CK(dalloc(&es, cap));
   CK(dalloc(&bins, cap));
@@ -246,10 +250,13 @@ int ensure_capacity(trinity_ctx* ctx, int need) {
     CK(cudaMemcpy(im, ctx->d_iters_max, ctx->capacity * sizeof(int), cudaMemcpyDeviceToDevice));
     CK(cudaMemcpy(is, ctx->d_iters_sum, ctx->capacity * sizeof(unsigned long long),
                   cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(ti, ctx->d_tile_iters, ctx->capacity * sizeof(unsigned long long),
+                  cudaMemcpyDeviceToDevice));
     CK(cudaMemcpy(en, ctx->d_energy, ctx->capacity * sizeof(double), cudaMemcpyDeviceToDevice));
     CK(cudaMemcpy(es, ctx->d_escaped, ctx->capacity * sizeof(double), cudaMemcpyDeviceToDevice));
     cudaFree(ctx->d_iters_max);
     cudaFree(ctx->d_iters_sum);
+    cudaFree(ctx->d_tile_iters);
     cudaFree(ctx->d_energy);
     cudaFree(ctx->d_escaped);
     cudaFree(ctx->d_bins);
@@ -264,6 +271,7 @@ int ensure_capacity(trinity_ctx* ctx, int need) {
   CK(cudaMemcpy(bins, hb.data(), cap * sizeof(int), cudaMemcpyHostToDevice));
   ctx->d_iters_max = im;
   ctx->d_iters_sum = is;
+  ctx->d_tile_iters = ti;
   ctx->d_energy = en;
   ctx->d_escaped = es;
   ctx->d_bins = bins;
@@ -1006,11 +1014,13 @@ int trinity_set_bins(trinity_ctx* ctx, double bin_ps, int nbins) {
     ctx->capacity = 0;
     cudaFree(ctx->d_iters_max);
     cudaFree(ctx->d_iters_sum);
+    cudaFree(ctx->d_tile_iters);
     cudaFree(ctx->d_energy);
     cudaFree(ctx->d_escaped);
     cudaFree(ctx->d_bins);
     ctx->d_iters_max = nullptr;
     ctx->d_iters_sum = nullptr;
+    ctx->d_tile_iters = nullptr;
     ctx->d_energy = nullptr;
     ctx->d_escaped = nullptr;
     ctx->d_bins = nullptr;
@@ -1255,6 +1265,7 @@ int adjoint_impl(trinity_ctx* ctx, const double* dL_dE, size_t n, double* grad_m
   RunState rs = run_state(ctx);  // recomputed steps: same step counter, smax and bins
   rs.iters_max = ctx->d_re_iters_max;
   rs.iters_sum = ctx->d_re_iters_sum;
+  rs.tile_iters = nullptr;
   rs.energy = ctx->d_re_energy;
   rs.escaped = ctx->d_re_escaped;
   rs.nonconv = ctx->d_re_nonconv;
@@ -1430,6 +1441,18 @@ int trinity_read_iterations(trinity_ctx* ctx, int* iters_max, double* iters_mean
   return TRINITY_OK;
 }
 
+int trinity_read_executed_iterations(trinity_ctx* ctx, double* executed_mean, size_t nsteps) {
+  if (!ctx || !executed_mean) return TRINITY_E_INVALID;
+  if (nsteps > static_cast<size_t>(ctx->steps_done)) return fail(ctx, TRINITY_E_INVALID, "more steps than done");
+  if (nsteps == 0) return TRINITY_OK;
+  const size_t first = ctx->steps_done - nsteps;
+  CK(cudaStreamSynchronize(ctx->stream));
+  std::vector<unsigned long long> t(nsteps);
+  CK(cudaMemcpy(t.data(), ctx->d_tile_iters + first, nsteps * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+  for (size_t k2 = 0; k2 < nsteps; ++k2) executed_mean[k2] = double(t[k2]) / double(ctx->g.nv);
+  return TRINITY_OK;
+}
+
 int trinity_read_field(trinity_ctx* ctx, int what, int back, void* out, size_t bytes, int ptr_kind) {
   if (!ctx) return TRINITY_E_INVALID;
   const size_t cnt = static_cast<size_t>(what == TRINITY_FIELD_S ? ctx->na_s : ctx->g.na) * ctx->g.nv;
@@ -1477,6 +1500,7 @@ int trinity_reset(trinity_ctx* ctx) {
   if (ctx->capacity > 0) {
     CK(cudaMemset(ctx->d_iters_max, 0, ctx->capacity * sizeof(int)));
     CK(cudaMemset(ctx->d_iters_sum, 0, ctx->capacity * sizeof(unsigned long long)));
+    CK(cudaMemset(ctx->d_tile_iters, 0, ctx->capacity * sizeof(unsigned long long)));
     CK(cudaMemset(ctx->d_energy, 0, ctx->capacity * sizeof(double)));
     CK(cudaMemset(ctx->d_escaped, 0, ctx->capacity * sizeof(double)));
   }
@@ -1515,7 +1539,7 @@ void trinity_destroy(trinity_ctx* ctx) {
                   ctx->nidx,      ctx->P32,        ctx->Pbf,         ctx->d_dirs,    ctx->d_offs,
                   ctx->d_det_vox, ctx->d_det_dir,  ctx->d_det_id,    ctx->d_det_w,   ctx->d_det,
                   ctx->d_step,    ctx->d_smax,     ctx->d_nonconv,   ctx->d_error,   ctx->d_iters_max,
-                  ctx->d_iters_sum, ctx->d_energy, ctx->d_escaped,   ctx->d_bins,
+                  ctx->d_iters_sum, ctx->d_energy, ctx->d_escaped,   ctx->d_bins, ctx->d_tile_iters,
                   ctx->d_tile_ctr, ctx->d_rcorr,   ctx->d_cls,       ctx->d_cls_ds,
                   ctx->d_rcorr32};
   for (void* p : bufs)

@@ -44,6 +44,8 @@ struct RunState {
   int* bins;                     // [capacity] detector bin of each step (-1: none)
   int* error;                    // device error word (0 = ok)
   int* tile_ctr;                 // [2] work counters of the persistent kernels (ping-pong)
+  unsigned long long* tile_iters; // [capacity] iterations executed x voxels per tile, summed
+                                  // (tensor-core kernel; null: not counted)
 };
 
 // Tables of the tensor-core source iteration.

@@ -581,6 +581,11 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
         atomicMax(rs.iters_max + n, im);
         atomicAdd(rs.iters_sum + n, is);
       }
+      // iterations the tile executed (its slowest voxel's) for each of its voxels
+      if (tid == 0 && rs.tile_iters) {
+        const int rows = g.nv - v0 < kM ? g.nv - v0 : kM;
+        atomicAdd(rs.tile_iters + n, static_cast<unsigned long long>(k) * rows);
+      }
     }
     __syncthreads();
   }
