@@ -85,3 +85,68 @@ def test_exact_rejects_continuous_optics_and_two_level_grids():
     q["nside_scatter"] = 2
     with pytest.raises(P.TrinityError, match="E_UNSUPPORTED"):
         P.Forward(dict(q, exact=True))
+
+
+def _sampled_one_step(prob, steps, vox, tol_scale=DET_TOL):
+    """Run ``steps`` steps on the GPU and recompute level steps-1 at ``vox`` with the oracle
+    from the GPU's own stored history (one step of Eq. 10, the interface split and the
+    source function converged to 1e-10, i.e. the fixed point the exact solve reaches)."""
+    P = _lib()
+    from oracle.solver import Model, one_step_at
+    fw = P.Forward(prob)
+    fw.step(steps)
+    n = steps - 1
+    hist = {}
+    for back in range(1, 5):
+        if n - back >= 0:
+            hist[n - back] = (fw.field(P.FIELD_I, back), fw.field(P.FIELD_S, back))
+    I_n, S_n = fw.field(P.FIELD_I, 0), fw.field(P.FIELD_S, 0)
+    fw.close()
+
+    def h(which, lev, d, u):
+        out = np.zeros(np.shape(lev))
+        for L, (Ia, Sa) in hist.items():
+            m = lev == L
+            if np.any(m):
+                out[m] = (Ia if which == "I" else Sa)[d[m], u[m]]
+        return out
+
+    s_glob = float(np.abs(hist[n - 1][1]).max())
+    p = dict(prob, tol=1e-10, max_iters=20000)
+    I_ref, S_ref, _ = one_step_at(Model(p), n, h, np.asarray(vox), s_glob)
+    assert np.abs(I_n[:, vox] - I_ref).max() <= tol_scale * np.abs(I_n).max()
+    assert np.abs(S_n[:, vox] - S_ref).max() <= tol_scale * np.abs(S_n).max()
+
+
+def test_full_size_slab_exact_sampled_one_step():
+    """The bench's exact-solve workload at full size (96x96x64, 192 directions)."""
+    prob = W.config_slab(steps=24)
+    prob["exact"] = True
+    nz, ny, nx = prob["nz"], prob["ny"], prob["nx"]
+    rng = np.random.default_rng(5)
+    cx, cy = nx // 2, ny // 2
+    vox = sorted({(z * ny + y) * nx + x for z, y, x in zip(rng.integers(0, 12, 64), rng.integers(cy - 8, cy + 8, 64),
+                                                           rng.integers(cx - 8, cx + 8, 64))} | {cy * nx + cx})
+    _sampled_one_step(prob, 24, vox)
+
+
+def test_full_size_phantom_exact_sampled_one_step():
+    """The heterogeneous phantom at full size (128x128x96, 192 directions, five optics
+    classes, refraction at the air cylinder): voxels near the source, in and beside the
+    cylinder and in the spheres, some in tiles that mix classes."""
+    prob = W.config_hetero(steps=20, precision="fp32")
+    prob["exact"] = True
+    nz, ny, nx = prob["nz"], prob["ny"], prob["nx"]
+    rng = np.random.default_rng(6)
+    zc, yc = nz // 2, ny // 2
+    vox = {(zc * ny + yc) * nx + 0}
+    vox |= {(z * ny + y) * nx + x for z, y, x in zip(rng.integers(zc - 6, zc + 6, 48),
+                                                      rng.integers(yc - 6, yc + 6, 48), rng.integers(0, 10, 48))}
+    cyl = prob["cylinder"]
+    for k in range(16):  # along the cylinder wall
+        x = int(cyl["center"][0] + (cyl["radius"] + 0.5) * np.cos(k)) % nx
+        y = int(cyl["center"][1] + (cyl["radius"] + 0.5) * np.sin(k)) % ny
+        vox.add((int(rng.integers(0, nz)) * ny + y) * nx + x)
+    for c, r, _ in prob["spheres"]:
+        vox.add((int(c[2]) * ny + int(c[1])) * nx + int(c[0]))
+    _sampled_one_step(prob, 20, sorted(vox))
