@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(GridParams g, const DirInfo*
 // max over directions of |S_new - S_old| and |S_new|: a warp "transpose" reduction leaves
 // lane v holding the warp's maximum for voxel v, then the warps combine through smem.
 // ----------------------------------------------------------------------------------------
-constexpr int kTile = 32;
+constexpr int kTile = 16;  // voxels per CTA: small enough for two CTAs per SM
 constexpr int kXStride = kTile + 4;  // padded row (floats) of the X tile in smem
 
 template <int NA>
@@ -146,10 +146,18 @@ struct ScatterCfg {
   static constexpr int kWarps = kThreads / 32;
 };
 
-// After the call lane l holds max over the warp's lanes of vals[l] (vals[0] on return).
-__device__ __forceinline__ float warp_transpose_max(float (&vals)[32], int lane) {
+// After the call lane l holds the max over the warp's lanes of vals[l mod V] (returned):
+// lanes l and l ^ s for s >= V first combine all V values, then a butterfly halves the
+// values each lane keeps while transposing them across lanes.
+template <int V>
+__device__ __forceinline__ float warp_transpose_max(float (&vals)[V], int lane) {
 #pragma unroll
-  for (int s = 16; s >= 1; s >>= 1) {
+  for (int s = 16; s >= V; s >>= 1) {
+#pragma unroll
+    for (int k = 0; k < V; ++k) vals[k] = fmaxf(vals[k], __shfl_xor_sync(0xffffffffu, vals[k], s));
+  }
+#pragma unroll
+  for (int s = V / 2; s >= 1; s >>= 1) {
     const bool upper = (lane & s) != 0;
 #pragma unroll
     for (int k = 0; k < s; ++k) {
@@ -163,7 +171,7 @@ __device__ __forceinline__ float warp_transpose_max(float (&vals)[32], int lane)
 }
 
 template <int NA>
-__global__ void __launch_bounds__(ScatterCfg<NA>::kThreads)
+__global__ void __launch_bounds__(ScatterCfg<NA>::kThreads, 2)
     scatter_fp32_kernel(GridParams g, const float* __restrict__ b1ds, int nch, const float* __restrict__ P,
                         const float* __restrict__ rcorr, const float* __restrict__ Q,
                         const float* __restrict__ mut, const float* __restrict__ eps,
@@ -172,8 +180,8 @@ __global__ void __launch_bounds__(ScatterCfg<NA>::kThreads)
                         int max_iters, RunState rs) {
   constexpr int W = ScatterCfg<NA>::kWarps;
   __shared__ __align__(16) float Xs[2][NA][kXStride];
-  __shared__ float red_d[W][kTile];
-  __shared__ float red_s[W][kTile];
+  __shared__ float red_d[W][32];  // per warp, lane v < kTile holds voxel v's reduction
+  __shared__ float red_s[W][32];
   __shared__ float e_s[kTile], rho_s[kTile], best_s[kTile];
   __shared__ int iters_s[kTile], stall_s[kTile];
   __shared__ unsigned act_s;
@@ -201,7 +209,8 @@ __global__ void __launch_bounds__(ScatterCfg<NA>::kThreads)
     best_s[tid] = 3.0e38f;
     stall_s[tid] = 0;
   }
-  if (tid == 0) act_s = (g.nv - v0 >= kTile) ? 0xffffffffu : ((1u << (g.nv - v0)) - 1u);
+  if (tid == 0)
+    act_s = (g.nv - v0 >= kTile) ? (kTile == 32 ? 0xffffffffu : ((1u << kTile) - 1u)) : ((1u << (g.nv - v0)) - 1u);
   __syncthreads();
 
   float q[kTile], b1[kTile], so[kTile], acc[kTile];
@@ -295,10 +304,10 @@ __global__ void __launch_bounds__(ScatterCfg<NA>::kThreads)
     red_d[warp][lane] = warp_transpose_max(dsv, lane);
     red_s[warp][lane] = warp_transpose_max(smv, lane);
     __syncthreads();
-    if (tid < kTile) {
+    if (tid < 32) {  // one full warp: the ballot below is warp-collective
       const int v = tid;
       unsigned done = 0u;
-      if ((act >> v) & 1u) {
+      if (v < kTile && ((act >> v) & 1u)) {
         float D = 0.0f, Sm = 0.0f;
 #pragma unroll
         for (int w = 0; w < W; ++w) {
