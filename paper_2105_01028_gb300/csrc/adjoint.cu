@@ -67,11 +67,21 @@ __device__ __forceinline__ float ray_db0(float x, float T) {
   return (T * (1.0f + x + x * x) - 1.0f) / (x * x);
 }
 
-// After the call lane l holds the warp's reduction of vals[l] (returned).
-template <bool kMax>
-__device__ __forceinline__ float warp_transpose(float (&vals)[32], int lane) {
+// After the call lane l holds the warp's reduction of vals[l mod V] (returned): lanes l
+// and l ^ s for s >= V first combine all V values, then a butterfly halves the values each
+// lane keeps while transposing them across lanes.
+template <bool kMax, int V>
+__device__ __forceinline__ float warp_transpose(float (&vals)[V], int lane) {
 #pragma unroll
-  for (int s = 16; s >= 1; s >>= 1) {
+  for (int s = 16; s >= V; s >>= 1) {
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      const float recv = __shfl_xor_sync(0xffffffffu, vals[k], s);
+      vals[k] = kMax ? fmaxf(vals[k], recv) : vals[k] + recv;
+    }
+  }
+#pragma unroll
+  for (int s = V / 2; s >= 1; s >>= 1) {
     const bool upper = (lane & s) != 0;
 #pragma unroll
     for (int k = 0; k < s; ++k) {
@@ -103,13 +113,13 @@ __global__ void adj_inject_kernel(const int* __restrict__ det_vox, const int* __
 
 // ----------------------------------------------------------------------------------------
 // Transposed scattering solve, FP32 on CUDA cores.  Same tiling and iteration as the
-// forward FP32 kernel (a CTA owns 32 voxels, thread i owns direction i, blocked sums of
+// forward FP32 kernel (a CTA owns 16 voxels, thread i owns direction i, blocked sums of
 // P X with the diagonal row-sum correction r_i, y = (1 - eps) (P X + r X), the same stop
 // rule with a stall exit) with q = Sbar_n + b1 Ibar_n and a warm start from the previous
 // reverse step's y.  The epilogue writes Qbar = Ibar_n + y, clears the consumed adjoint
 // level, and adds the voxel's dL/da and the b1 part of dL/dmu_t to the FP64 sums.
 // ----------------------------------------------------------------------------------------
-constexpr int kTile = 32;
+constexpr int kTile = 16;  // voxels per CTA: small enough for two CTAs per SM
 constexpr int kXStride = kTile + 4;
 
 template <int NA>
@@ -119,7 +129,7 @@ struct AdjCfg {
 };
 
 template <int NA>
-__global__ void __launch_bounds__(AdjCfg<NA>::kThreads)
+__global__ void __launch_bounds__(AdjCfg<NA>::kThreads, 2)
     adj_scatter_fp32_kernel(int nv, const DirInfo* __restrict__ dirs, float ds_max,
                             const float* __restrict__ P, const float* __restrict__ rcorr,
                             const float* __restrict__ mut, const float* __restrict__ eps,
@@ -131,8 +141,8 @@ __global__ void __launch_bounds__(AdjCfg<NA>::kThreads)
                             int* nonconv, unsigned long long* iters_sum) {
   constexpr int W = AdjCfg<NA>::kWarps;
   __shared__ __align__(16) float Xs[2][NA][kXStride];
-  __shared__ float red_d[W][kTile];
-  __shared__ float red_s[W][kTile];
+  __shared__ float red_d[W][32];  // per warp, lane v < kTile holds voxel v's reduction
+  __shared__ float red_s[W][32];
   __shared__ float e_s[kTile], rho_s[kTile], best_s[kTile];
   __shared__ int stall_s[kTile], iters_s[kTile];
   __shared__ unsigned act_s;
@@ -159,7 +169,8 @@ __global__ void __launch_bounds__(AdjCfg<NA>::kThreads)
     stall_s[tid] = 0;
     iters_s[tid] = 0;
   }
-  if (tid == 0) act_s = (nv - v0 >= kTile) ? 0xffffffffu : ((1u << (nv - v0)) - 1u);
+  if (tid == 0)
+    act_s = (nv - v0 >= kTile) ? (kTile == 32 ? 0xffffffffu : ((1u << kTile) - 1u)) : ((1u << (nv - v0)) - 1u);
   __syncthreads();
 
   float q[kTile], b1[kTile], so[kTile], acc[kTile];
@@ -241,10 +252,10 @@ __global__ void __launch_bounds__(AdjCfg<NA>::kThreads)
     red_d[warp][lane] = warp_transpose<true>(dsv, lane);
     red_s[warp][lane] = warp_transpose<true>(smv, lane);
     __syncthreads();
-    if (tid < kTile) {
+    if (tid < 32) {  // one full warp: the ballot below is warp-collective
       const int v = tid;
       unsigned done = 0u;
-      if ((act >> v) & 1u) {
+      if (v < kTile && ((act >> v) & 1u)) {
         float D = 0.0f, Sm = 0.0f;
 #pragma unroll
         for (int w = 0; w < W; ++w) {
