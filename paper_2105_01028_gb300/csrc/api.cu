@@ -669,6 +669,8 @@ int trinity_create_grid(const trinity_grid_desc* desc, void* cuda_stream, trinit
   ctx->dt = desc->courant * desc->h_mm * desc->n_ref / kC0;
   ctx->w = 4.0 * 3.14159265358979323846 / g.na;
   g.e_scale = static_cast<float>(desc->h_mm * desc->h_mm * desc->h_mm / kC0 * ctx->w);
+  g.mut_u = -1.0f;
+  g.n_u = 0.0f;
   try {
     ctx->dirs = healpix_dirs(desc->nside);
     ctx->lat = build_lattice(ctx->dirs, g.nx, g.ny, g.nz, desc->h_mm, g.periodic != 0);
@@ -868,6 +870,15 @@ int trinity_set_optics(trinity_ctx* ctx, const float* mua, const float* mus, con
   CK(cudaMemcpy(ctx->Pbf, Pb.data(), Pb.size() * 2, cudaMemcpyHostToDevice));
   ctx->g_aniso = g;
   ctx->optics_set = true;
+  // A uniform mu_t or n lets the sweeps take exp, b0, b1 and the retarded delay once per
+  // direction instead of once per voxel (the same FP32 operations on the same values).
+  const auto same_bits = [](const std::vector<float>& x) {
+    return std::all_of(x.begin(), x.end(), [&](float y) { return std::memcmp(&y, &x[0], 4) == 0; });
+  };
+  ctx->g.mut_u = same_bits(mt) ? mt[0] : -1.0f;
+  ctx->g.n_u = same_bits(r) ? r[0] : 0.0f;
+  ctx->g_s.mut_u = ctx->g.mut_u;
+  ctx->g_s.n_u = ctx->g.n_u;
   ctx->nmap = r;
   ctx->h_P32 = P32;
   ctx->h_rc32 = rc;

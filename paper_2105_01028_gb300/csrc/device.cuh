@@ -30,6 +30,8 @@ struct GridParams {
   float h;
   float ds_max;     // max_d ds_d (for the contraction bound)
   float e_scale;    // h^3 / c0 * w  (energy per unit I * n)
+  float mut_u;      // mu_t of every voxel when the medium's mu_t is uniform, else -1
+  float n_u;        // n of every voxel when the refractive index is uniform, else 0
 };
 
 // Per-run device counters and tallies (pointers into context-owned buffers).

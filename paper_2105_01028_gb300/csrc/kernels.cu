@@ -1,6 +1,6 @@
-// FP32 kernels of one time step: the ray sweep (Eq. 10 without its S(n) term), the
-// per-voxel source iteration on CUDA cores (Eq. 12, Section 2.4 steps 5-6), the
-// detector / escape tallies (Section 3.1) and the step counter.
+// FP32 kernels of one time step: the per-voxel source iteration on CUDA cores (Eq. 12,
+// Section 2.4 steps 5-6), the detector / escape tallies (Section 3.1), the interface
+// split and the step counter.
 #include <cfloat>
 #include <cstdint>
 
@@ -15,120 +15,8 @@ __device__ __forceinline__ int pick(int axis, int x, int y, int z) {
 }
 
 // ----------------------------------------------------------------------------------------
-// Sweep: Q(v, d) = I_up exp(-x) + S_up b0(x), the known part of Eq. 10 at time level n.
-// The upwind sample of v is the previous point of its long ray (slab lattice, Section
-// 2.1): one slab back along dom(d), shifted by the per-slab offsets.  Its I and S are
-// taken at the retarded time n - delta, delta = ds n(v) / (c0 dt), linearly
-// interpolated between the stored levels n - m and n - m - 1 (m = floor(delta)).
-//
-// Mapping: blockIdx.y = direction; a block covers whole x-rows (threadIdx.x along x,
-// threadIdx.y one row each), so a warp reads contiguous, at most one-voxel-shifted runs
-// of the upwind plane.  The direction's constants are staged in shared memory once per
-// block, and the lattice offsets are uniform along a row unless x is the dominant axis.
-// The block also resolves, once, where the five stored levels n - m (m = 0..4) of this
-// direction's plane live, so a voxel indexes them by its delay's whole part m.
-// ----------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) sweep_kernel(GridParams g, const DirInfo* __restrict__ dirs,
-                                                    const int8_t* __restrict__ offs,
-                                                    const float* __restrict__ Iring,
-                                                    const float* __restrict__ Sring,
-                                                    const float* __restrict__ mut,
-                                                    const float* __restrict__ nidx,
-                                                    float* __restrict__ Q, RunState rs) {
-  __shared__ DirInfo di_s;
-  __shared__ int n_s;
-  __shared__ const float* ilev_s[5];  // plane d of I at level n - m, null before the history
-  __shared__ const float* slev_s[5];
-  const int d = blockIdx.y;
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  if (tid == 0) {
-    di_s = dirs[d];
-    n_s = *rs.step;
-    if (d == 0 && blockIdx.x == 0) {
-      rs.smax[n_s & 1] = 0u;     // max |S(n)|, filled by this step's source iteration
-      rs.tile_ctr[n_s & 1] = 0;  // work counter of this step's persistent kernel
-    }
-  }
-  __syncthreads();
-  if (tid < 5) {
-    const int L = n_s - tid;
-    const size_t o = (static_cast<size_t>(ring_slot(L)) * g.na + d) * static_cast<size_t>(g.nv);
-    ilev_s[tid] = L >= g.hist_from ? Iring + o : nullptr;
-    slev_s[tid] = L >= g.hist_from ? Sring + o : nullptr;
-  }
-  __syncthreads();
-  const int row = blockIdx.x * blockDim.y + threadIdx.y;  // (y, z) row index
-  if (row >= g.ny * g.nz) return;
-  const int n = n_s;
-  const int dom = di_s.dom, sgn = di_s.sgn, a0 = di_s.a0, a1 = di_s.a1;
-  const float ds = di_s.ds, dc_hi = di_s.dcoef, dc_lo = di_s.dcoef_lo, src_amp = di_s.src_amp;
-  const int y = row % g.ny, z = row / g.ny;
-  const size_t plane = static_cast<size_t>(g.nv);
-  const int8_t* off0 = offs + (static_cast<size_t>(d) * 2 + 0) * g.nmax;
-  const int8_t* off1 = offs + (static_cast<size_t>(d) * 2 + 1) * g.nmax;
-  const int nd = pick(dom, g.nx, g.ny, g.nz);
-  const int n0 = pick(a0, g.nx, g.ny, g.nz);
-  const int n1 = pick(a1, g.nx, g.ny, g.nz);
-  const int sd = dom == 0 ? 1 : (dom == 1 ? g.nx : g.nx * g.ny);
-  const int s0 = a0 == 0 ? 1 : (a0 == 1 ? g.nx : g.nx * g.ny);
-  const int s1 = a1 == 0 ? 1 : (a1 == 1 ? g.nx : g.nx * g.ny);
-  const size_t lev0 = static_cast<size_t>(d) * plane;
-  const size_t row_base = static_cast<size_t>(row) * g.nx;
-
-  for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
-    const size_t v = row_base + x;
-    const int pd = pick(dom, x, y, z);
-    const int p0 = pick(a0, x, y, z);
-    const int p1 = pick(a1, x, y, z);
-    const int kp = sgn > 0 ? pd : nd - 1 - pd;
-    int qd = pd - sgn;
-    int q0 = p0 - off0[kp];
-    int q1 = p1 - off1[kp];
-    int kind = 0;  // 0: upwind inside, 1: inflow face, 2: entered through a side face
-    if (g.periodic) {
-      qd = (qd + nd) % nd;
-      q0 = (q0 + n0) % n0;
-      q1 = (q1 + n1) % n1;
-    } else if (kp == 0) {
-      kind = 1;
-    } else if (q0 < 0 || q0 >= n0 || q1 < 0 || q1 >= n1) {
-      kind = 2;
-    }
-    int m;
-    float f;
-    retarded_delay(dc_hi, dc_lo, __ldg(nidx + v), m, f);
-    m = m < 1 ? 1 : (m > 3 ? 3 : m);  // the optics check keeps every delay in [1, 4)
-    const int L0 = n - m, L1 = n - m - 1;
-    float Iup = 0.0f, Sup = 0.0f;
-    if (kind == 0) {
-      const int u = qd * sd + q0 * s0 + q1 * s1;  // < nv <= 2^30
-      const float* i0p = ilev_s[m];
-      const float* i1p = ilev_s[m + 1];
-      float i0 = 0.0f, i1 = 0.0f, s0v = 0.0f, s1v = 0.0f;
-      if (i0p) {
-        i0 = __ldg(i0p + u);
-        s0v = __ldg(slev_s[m] + u);
-      }
-      if (i1p) {
-        i1 = __ldg(i1p + u);
-        s1v = __ldg(slev_s[m + 1] + u);
-      }
-      Iup = (1.0f - f) * i0 + f * i1;
-      Sup = (1.0f - f) * s0v + f * s1v;
-    } else if (kind == 1 && static_cast<int>(v) == g.src_voxel && src_amp != 0.0f) {
-      const float on0 = (L0 >= 0 && L0 < g.pulse_steps) ? 1.0f : 0.0f;
-      const float on1 = (L1 >= 0 && L1 < g.pulse_steps) ? 1.0f : 0.0f;
-      Iup = src_amp * ((1.0f - f) * on0 + f * on1);
-    }
-    const float xo = __ldg(mut + v) * ds;
-    const float T = expf(-xo);
-    Q[lev0 + v] = Iup * T + Sup * ray_b0(xo, T);
-  }
-}
-
-// ----------------------------------------------------------------------------------------
 // Source iteration on CUDA cores (plain FP32 mode).
-// A CTA owns a tile of 32 voxels; thread i < NA owns outgoing direction i of all 32.
+// A CTA owns a tile of kTile voxels; thread i < NA owns outgoing direction i of all of them.
 // Per iteration: Y[v][i] = sum_j P[i][j] X[v][j] + r_i X[v][i] (P symmetric, read as
 // P[j][i] so a warp reads a contiguous row; r_i = 1 - sum_j P[i][j] restores the unit row
 // and column sums that FP32 rounding of P breaks), S_new = (1 - eps) Y with
@@ -485,19 +373,6 @@ __global__ void __launch_bounds__(32 * kIfaceWarps)
 }
 
 }  // namespace
-
-cudaError_t launch_sweep(const GridParams& g, const DirInfo* dirs, const int8_t* offs,
-                         const float* Iring, const float* Sring, const float* mut,
-                         const float* nidx, float* Q, RunState rs, cudaStream_t st) {
-  int bx = ((g.nx + 31) / 32) * 32;
-  if (bx > 256) bx = 256;
-  const int by = 256 / bx;
-  const int rows = g.ny * g.nz;
-  dim3 block(bx, by);
-  dim3 grid((rows + by - 1) / by, g.na);
-  sweep_kernel<<<grid, block, 0, st>>>(g, dirs, offs, Iring, Sring, mut, nidx, Q, rs);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_scatter_fp32(const GridParams& g, const float* b1ds, int nch, const float* P,
                                 const float* rcorr, const float* Q, const float* mut,

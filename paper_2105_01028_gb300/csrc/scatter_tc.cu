@@ -23,6 +23,10 @@
 // Thread mapping: 16 warps (12 for 48 directions); warp w reads TMEM lanes 32 (w % 4) ..
 // + 31 (one voxel row per thread) and the column group w / 4 (a quarter / third of the
 // directions).
+// Tiles are 8 x 4 x 4 voxel bricks (row r: x + (r & 7), y + (r >> 3 & 3), z + (r >> 5)):
+// a tile iterates until its slowest voxel stops, and the iteration count varies smoothly
+// in space, so a compact brick wastes fewer iterations than a run of 128 voxels along x.
+// A warp's 32 rows are four 8-voxel x-runs: 32-byte sectors, as coalesced as one run.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -203,6 +207,17 @@ __device__ __forceinline__ uint32_t sw128_chunk_off(int rows, int r, int k0) {
   return static_cast<uint32_t>(kb * rows * 128 + r * 128 + ((ch ^ (r & 7)) << 4));
 }
 
+// Flat voxel index of row r of brick tile ``tile`` (bricks numbered x fastest), -1 outside.
+__device__ __forceinline__ int brick_voxel(const GridParams& g, int bxn, int byn, int tile, int r) {
+  const int bx = tile % bxn, t2 = tile / bxn;
+  const int x = (bx << 3) + (r & 7), y = ((t2 % byn) << 2) + ((r >> 3) & 3), z = ((t2 / byn) << 2) + (r >> 5);
+  return (x < g.nx && y < g.ny && z < g.nz) ? (z * g.ny + y) * g.nx + x : -1;
+}
+
+__host__ __device__ __forceinline__ int brick_tiles(int nx, int ny, int nz) {
+  return ((nx + 7) >> 3) * ((ny + 3) >> 2) * ((nz + 3) >> 2);
+}
+
 // Shared-memory vector loads issued as volatile asm: the tables they read are constant
 // over the iteration loop, and without this the compiler hoists every chunk's values
 // out of the loop into registers (far more than the register budget).
@@ -313,7 +328,8 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
   const bool has_prev = (n - 1) >= g.hist_from;
   const size_t prev_base = static_cast<size_t>(ring_slot(n - 1)) * g.na * plane;
   const size_t cur_base = static_cast<size_t>(ring_slot(n)) * g.na * plane;
-  const int ntiles = (g.nv + kM - 1) / kM;
+  const int bxn = (g.nx + 7) >> 3, byn = (g.ny + 3) >> 2;
+  const int ntiles = brick_tiles(g.nx, g.ny, g.nz);
 
   // ---- one-time set-up: TMEM, barrier, B operand, correction and class tables
   if (warp == 0) tmem_alloc(&tmem_base_s, C::TCOLS);
@@ -355,15 +371,15 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
     __syncthreads();
     const int tile = tile_s;
     if (tile >= ntiles) break;
-    const int v0 = tile * kM;
-    const int v = v0 + row;
-    const bool vin = v < g.nv;
+    const int vb = brick_voxel(g, bxn, byn, tile, row);
+    const bool vin = vb >= 0;
+    const int v = vin ? vb : 0;
 
     // per-row constants and the b1 table over ds classes
     if (tid < kM) {
-      const int vv = v0 + tid;
+      const int vv = brick_voxel(g, bxn, byn, tile, tid);
       float ev = 1.0f, rho = 0.0f;
-      if (vv < g.nv) {
+      if (vv >= 0) {
         ev = eps[vv];
         const float xm = mut[vv] * g.ds_max;
         rho = (1.0f - ev) * ray_b1(xm, expf(-xm));
@@ -375,9 +391,9 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
     // coarse direction's children (b1 is then their mean)
     for (int u = tid; u < ncls * kM; u += blockDim.x) {
       const int k = u / kM, r = u % kM;
-      const int vv = v0 + r;
+      const int vv = brick_voxel(g, bxn, byn, tile, r);
       float bs = 0.0f;
-      if (vv < g.nv) {
+      if (vv >= 0) {
         const float mu = mut[vv];
         for (int j = 0; j < nch; ++j) {
           const float x = mu * cls_ds[k * nch + j];
@@ -582,10 +598,9 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
         atomicAdd(rs.iters_sum + n, is);
       }
       // iterations the tile executed (its slowest voxel's) for each of its voxels
-      if (tid == 0 && rs.tile_iters) {
-        const int rows = g.nv - v0 < kM ? g.nv - v0 : kM;
+      const int rows = __popc(__ballot_sync(0xffffffffu, vin));
+      if (lane == 0 && rs.tile_iters && rows > 0)
         atomicAdd(rs.tile_iters + n, static_cast<unsigned long long>(k) * rows);
-      }
     }
     __syncthreads();
   }
@@ -719,7 +734,7 @@ bool scatter_bf16_supported(int na) {
 cudaError_t launch_scatter_bf16(const GridParams& g, const BfTables& t, const uint16_t* Pbf, const float* Q,
                                 const float* mut, const float* eps, const float* nidx, float* Iring,
                                 float* Sring, float tol, int max_iters, RunState rs, cudaStream_t st) {
-  const int ntiles = (g.nv + kM - 1) / kM;
+  const int ntiles = brick_tiles(g.nx, g.ny, g.nz);
   const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
   if (g.na == 48) {
     scatter_tc_kernel<48><<<grid, Tc<48>::kThreads, Tc<48>::SMEM, st>>>(g, t.rcorr, t.cls, t.cls_ds, t.ncls, t.nch, Pbf, Q, mut,

@@ -22,6 +22,9 @@ __device__ __forceinline__ int pick(int axis, int x, int y, int z) {
 }
 
 // blockIdx.y = coarse direction c; a block covers whole x-rows as in the one-level sweep.
+// kUniN / kUniMu: uniform refractive index / mu_t, so each child's delay split (m, f) /
+// exp(-x) and b0(x) are taken once per block (same FP32 operations on the same values).
+template <bool kUniN, bool kUniMu>
 __global__ void __launch_bounds__(256) sweep2_kernel(GridParams g, const DirInfo* __restrict__ dirs,
                                                      const int8_t* __restrict__ offs,
                                                      const int* __restrict__ children, int nch, int na_s,
@@ -34,12 +37,30 @@ __global__ void __launch_bounds__(256) sweep2_kernel(GridParams g, const DirInfo
   extern __shared__ DirInfo ch_s[];  // the nch children's constants
   __shared__ int n_s;
   __shared__ int chd_s[64];
+  __shared__ int m_s[kUniN ? 64 : 1];
+  __shared__ float f_s[kUniN ? 64 : 1];
+  __shared__ float T_s[kUniMu ? 64 : 1];
+  __shared__ float b0_s[kUniMu ? 64 : 1];
   const int c = blockIdx.y;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   for (int k = tid; k < nch; k += blockDim.x * blockDim.y) {
     const int d = children[c * nch + k];
+    const DirInfo di = dirs[d];
     chd_s[k] = d;
-    ch_s[k] = dirs[d];
+    ch_s[k] = di;
+    if (kUniN) {
+      int m;
+      float f;
+      retarded_delay(di.dcoef, di.dcoef_lo, g.n_u, m, f);
+      m_s[k] = m;
+      f_s[k] = f;
+    }
+    if (kUniMu) {
+      const float xo = g.mut_u * di.ds;
+      const float T = expf(-xo);
+      T_s[k] = T;
+      b0_s[k] = ray_b0(xo, T);
+    }
   }
   if (tid == 0) {
     n_s = *rs.step;
@@ -62,8 +83,8 @@ __global__ void __launch_bounds__(256) sweep2_kernel(GridParams g, const DirInfo
 
   for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
     const size_t v = row_base + x;
-    const float mu = __ldg(mut + v);
-    const float nv_idx = __ldg(nidx + v);
+    const float mu = kUniMu ? 0.0f : __ldg(mut + v);
+    const float nv_idx = kUniN ? 0.0f : __ldg(nidx + v);
     float acc = 0.0f;
     for (int k = 0; k < nch; ++k) {
       const DirInfo& di = ch_s[k];
@@ -89,7 +110,12 @@ __global__ void __launch_bounds__(256) sweep2_kernel(GridParams g, const DirInfo
       }
       int m;
       float f;
-      retarded_delay(di.dcoef, di.dcoef_lo, nv_idx, m, f);
+      if (kUniN) {
+        m = m_s[k];
+        f = f_s[k];
+      } else {
+        retarded_delay(di.dcoef, di.dcoef_lo, nv_idx, m, f);
+      }
       const int L0 = n - m, L1 = n - m - 1;
       float Iup = 0.0f, Sup = 0.0f;
       if (kind == 0) {
@@ -114,9 +140,16 @@ __global__ void __launch_bounds__(256) sweep2_kernel(GridParams g, const DirInfo
         const float on1 = (L1 >= 0 && L1 < g.pulse_steps) ? 1.0f : 0.0f;
         Iup = di.src_amp * ((1.0f - f) * on0 + f * on1);
       }
-      const float xo = mu * di.ds;
-      const float T = expf(-xo);
-      const float q = Iup * T + Sup * ray_b0(xo, T);
+      float T, b0;
+      if (kUniMu) {
+        T = T_s[k];
+        b0 = b0_s[k];
+      } else {
+        const float xo = mu * di.ds;
+        T = expf(-xo);
+        b0 = ray_b0(xo, T);
+      }
+      const float q = Iup * T + Sup * b0;
       Qf[static_cast<size_t>(d) * plane + v] = q;
       acc += q;
     }
@@ -125,6 +158,8 @@ __global__ void __launch_bounds__(256) sweep2_kernel(GridParams g, const DirInfo
 }
 
 // I_f(n) = Q_f + b1_f S_c(n) for every child f of coarse direction c = blockIdx.y.
+// kUniMu: uniform mu_t, so each child's b1 is taken once per block.
+template <bool kUniMu>
 __global__ void __launch_bounds__(256) refine_kernel(GridParams g, const DirInfo* __restrict__ dirs,
                                                      const int* __restrict__ children, int nch, int na_s,
                                                      const float* __restrict__ mut,
@@ -133,13 +168,18 @@ __global__ void __launch_bounds__(256) refine_kernel(GridParams g, const DirInfo
                                                      float* __restrict__ Iring, RunState rs) {
   __shared__ int n_s;
   __shared__ int chd_s[64];
-  __shared__ float ds_s[64];
+  __shared__ float ds_s[64];  // the child's ds, or its b1 when mu_t is uniform
   const int c = blockIdx.y;
   const int tid = threadIdx.x;
   for (int k = tid; k < nch; k += blockDim.x) {
     const int d = children[c * nch + k];
     chd_s[k] = d;
-    ds_s[k] = dirs[d].ds;
+    if (kUniMu) {
+      const float xo = g.mut_u * dirs[d].ds;
+      ds_s[k] = ray_b1(xo, expf(-xo));
+    } else {
+      ds_s[k] = dirs[d].ds;
+    }
   }
   if (tid == 0) n_s = *rs.step;
   __syncthreads();
@@ -148,12 +188,18 @@ __global__ void __launch_bounds__(256) refine_kernel(GridParams g, const DirInfo
   const int n = n_s;
   const size_t plane = static_cast<size_t>(g.nv);
   const float s = Sring[(static_cast<size_t>(ring_slot(n)) * na_s + c) * plane + v];
-  const float mu = mut[v];
+  const float mu = kUniMu ? 0.0f : mut[v];
   float* Iout = Iring + static_cast<size_t>(ring_slot(n)) * g.na * plane;
   for (int k = 0; k < nch; ++k) {
     const size_t o = static_cast<size_t>(chd_s[k]) * plane + v;
-    const float xo = mu * ds_s[k];
-    Iout[o] = fmaf(ray_b1(xo, expf(-xo)), s, Qf[o]);
+    float b1;
+    if (kUniMu) {
+      b1 = ds_s[k];
+    } else {
+      const float xo = mu * ds_s[k];
+      b1 = ray_b1(xo, expf(-xo));
+    }
+    Iout[o] = fmaf(b1, s, Qf[o]);
   }
 }
 
@@ -184,8 +230,20 @@ cudaError_t launch_sweep2(const GridParams& g, const DirInfo* dirs, const int8_t
   const int rows = g.ny * g.nz;
   dim3 block(bx, by);
   dim3 grid((rows + by - 1) / by, na_s);
-  sweep2_kernel<<<grid, block, nch * sizeof(DirInfo), st>>>(g, dirs, offs, children, nch, na_s, Iring, Sring,
-                                                            mut, nidx, Qf, Qc, rs);
+  const size_t smem = nch * sizeof(DirInfo);
+  const bool un = g.n_u >= 1.0f, um = g.mut_u >= 0.0f;
+  if (un && um)
+    sweep2_kernel<true, true><<<grid, block, smem, st>>>(g, dirs, offs, children, nch, na_s, Iring, Sring, mut,
+                                                         nidx, Qf, Qc, rs);
+  else if (un)
+    sweep2_kernel<true, false><<<grid, block, smem, st>>>(g, dirs, offs, children, nch, na_s, Iring, Sring, mut,
+                                                          nidx, Qf, Qc, rs);
+  else if (um)
+    sweep2_kernel<false, true><<<grid, block, smem, st>>>(g, dirs, offs, children, nch, na_s, Iring, Sring, mut,
+                                                          nidx, Qf, Qc, rs);
+  else
+    sweep2_kernel<false, false><<<grid, block, smem, st>>>(g, dirs, offs, children, nch, na_s, Iring, Sring,
+                                                           mut, nidx, Qf, Qc, rs);
   return cudaGetLastError();
 }
 
@@ -194,7 +252,10 @@ cudaError_t launch_refine(const GridParams& g, const DirInfo* dirs, const int* c
                           cudaStream_t st) {
   if (nch < 1 || nch > 64) return cudaErrorInvalidValue;
   dim3 grid((g.nv + 255) / 256, na_s);
-  refine_kernel<<<grid, 256, 0, st>>>(g, dirs, children, nch, na_s, mut, Qf, Sring, Iring, rs);
+  if (g.mut_u >= 0.0f)
+    refine_kernel<true><<<grid, 256, 0, st>>>(g, dirs, children, nch, na_s, mut, Qf, Sring, Iring, rs);
+  else
+    refine_kernel<false><<<grid, 256, 0, st>>>(g, dirs, children, nch, na_s, mut, Qf, Sring, Iring, rs);
   return cudaGetLastError();
 }
 
