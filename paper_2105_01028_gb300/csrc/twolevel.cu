@@ -21,11 +21,27 @@ __device__ __forceinline__ int pick(int axis, int x, int y, int z) {
   return axis == 0 ? x : (axis == 1 ? y : z);
 }
 
-// blockIdx.y = coarse direction c; a block covers whole x-rows as in the one-level sweep.
+// One child direction's constants, staged in shared memory once per block.
+struct Child {
+  const float* ilev[5];  // plane d of I at level n - m (m = 0..4), null before the history
+  const int8_t* off0;    // per-slab lattice offsets along a0 and a1
+  const int8_t* off1;
+  float* qf;             // plane d of Q_f
+  int dom, sgn, a0, a1, nd, n0, n1, sd, s0, s1;
+  float ds, dc_hi, dc_lo, src_amp;
+  int m;                 // uniform refractive index: the delay's whole part ...
+  float f, T, b0;        // ... and fraction; uniform mu_t: exp(-x) and b0(x)
+};
+
+// blockIdx.y = coarse direction c; a block covers whole x-rows as in the one-level sweep
+// and strides over kRowSweeps2 groups of rows; each thread loops over the children of c
+// for its voxel, so the coarse mean is a register sum in the children table's order.
 // kUniN / kUniMu: uniform refractive index / mu_t, so each child's delay split (m, f) /
 // exp(-x) and b0(x) are taken once per block (same FP32 operations on the same values).
+constexpr int kRowSweeps2 = 4;
+
 template <bool kUniN, bool kUniMu>
-__global__ void __launch_bounds__(256) sweep2_kernel(GridParams g, const DirInfo* __restrict__ dirs,
+__global__ void __launch_bounds__(256, 5) sweep2_kernel(GridParams g, const DirInfo* __restrict__ dirs,
                                                      const int8_t* __restrict__ offs,
                                                      const int* __restrict__ children, int nch, int na_s,
                                                      const float* __restrict__ Iring,
@@ -34,34 +50,13 @@ __global__ void __launch_bounds__(256) sweep2_kernel(GridParams g, const DirInfo
                                                      const float* __restrict__ nidx,
                                                      float* __restrict__ Qf, float* __restrict__ Qc,
                                                      RunState rs) {
-  extern __shared__ DirInfo ch_s[];  // the nch children's constants
+  extern __shared__ uint8_t sm2[];
+  Child* cs = reinterpret_cast<Child*>(sm2);  // [nch]
   __shared__ int n_s;
-  __shared__ int chd_s[64];
-  __shared__ int m_s[kUniN ? 64 : 1];
-  __shared__ float f_s[kUniN ? 64 : 1];
-  __shared__ float T_s[kUniMu ? 64 : 1];
-  __shared__ float b0_s[kUniMu ? 64 : 1];
+  __shared__ const float* slev_s[5];  // plane c of coarse S at level n - m
   const int c = blockIdx.y;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  for (int k = tid; k < nch; k += blockDim.x * blockDim.y) {
-    const int d = children[c * nch + k];
-    const DirInfo di = dirs[d];
-    chd_s[k] = d;
-    ch_s[k] = di;
-    if (kUniN) {
-      int m;
-      float f;
-      retarded_delay(di.dcoef, di.dcoef_lo, g.n_u, m, f);
-      m_s[k] = m;
-      f_s[k] = f;
-    }
-    if (kUniMu) {
-      const float xo = g.mut_u * di.ds;
-      const float T = expf(-xo);
-      T_s[k] = T;
-      b0_s[k] = ray_b0(xo, T);
-    }
-  }
+  const size_t plane = static_cast<size_t>(g.nv);
   if (tid == 0) {
     n_s = *rs.step;
     if (c == 0 && blockIdx.x == 0) {
@@ -70,90 +65,129 @@ __global__ void __launch_bounds__(256) sweep2_kernel(GridParams g, const DirInfo
     }
   }
   __syncthreads();
-  const int row = blockIdx.x * blockDim.y + threadIdx.y;
-  if (row >= g.ny * g.nz) return;
   const int n = n_s;
-  const int y = row % g.ny, z = row / g.ny;
-  const size_t plane = static_cast<size_t>(g.nv);
-  const size_t row_base = static_cast<size_t>(row) * g.nx;
-  const float* Sc0 = Sring + static_cast<size_t>(c) * plane;  // plane c of a coarse level
-  const size_t slevel = static_cast<size_t>(na_s) * plane;
-  const size_t ilevel = static_cast<size_t>(g.na) * plane;
-  const float inv = 1.0f / static_cast<float>(nch);
-
-  for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
-    const size_t v = row_base + x;
-    const float mu = kUniMu ? 0.0f : __ldg(mut + v);
-    const float nv_idx = kUniN ? 0.0f : __ldg(nidx + v);
-    float acc = 0.0f;
-    for (int k = 0; k < nch; ++k) {
-      const DirInfo& di = ch_s[k];
-      const int d = chd_s[k];
-      const int dom = di.dom, sgn = di.sgn, a0 = di.a0, a1 = di.a1;
-      const int nd = pick(dom, g.nx, g.ny, g.nz);
-      const int n0 = pick(a0, g.nx, g.ny, g.nz);
-      const int n1 = pick(a1, g.nx, g.ny, g.nz);
-      const int pd = pick(dom, x, y, z), p0 = pick(a0, x, y, z), p1 = pick(a1, x, y, z);
-      const int kp = sgn > 0 ? pd : nd - 1 - pd;
-      int qd = pd - sgn;
-      int q0 = p0 - offs[(static_cast<size_t>(d) * 2 + 0) * g.nmax + kp];
-      int q1 = p1 - offs[(static_cast<size_t>(d) * 2 + 1) * g.nmax + kp];
-      int kind = 0;
-      if (g.periodic) {
-        qd = (qd + nd) % nd;
-        q0 = (q0 + n0) % n0;
-        q1 = (q1 + n1) % n1;
-      } else if (kp == 0) {
-        kind = 1;
-      } else if (q0 < 0 || q0 >= n0 || q1 < 0 || q1 >= n1) {
-        kind = 2;
-      }
+  if (tid < 5) {
+    const int L = n - tid;
+    slev_s[tid] = L >= g.hist_from ? Sring + (static_cast<size_t>(ring_slot(L)) * na_s + c) * plane : nullptr;
+  }
+  for (int k = tid; k < nch; k += blockDim.x * blockDim.y) {
+    const int d = children[c * nch + k];
+    const DirInfo di = dirs[d];
+    Child ch;
+    for (int mm = 0; mm < 5; ++mm) {
+      const int L = n - mm;
+      ch.ilev[mm] = L >= g.hist_from ? Iring + (static_cast<size_t>(ring_slot(L)) * g.na + d) * plane : nullptr;
+    }
+    ch.off0 = offs + (static_cast<size_t>(d) * 2 + 0) * g.nmax;
+    ch.off1 = offs + (static_cast<size_t>(d) * 2 + 1) * g.nmax;
+    ch.qf = Qf + static_cast<size_t>(d) * plane;
+    ch.dom = di.dom;
+    ch.sgn = di.sgn;
+    ch.a0 = di.a0;
+    ch.a1 = di.a1;
+    ch.nd = pick(di.dom, g.nx, g.ny, g.nz);
+    ch.n0 = pick(di.a0, g.nx, g.ny, g.nz);
+    ch.n1 = pick(di.a1, g.nx, g.ny, g.nz);
+    ch.sd = di.dom == 0 ? 1 : (di.dom == 1 ? g.nx : g.nx * g.ny);
+    ch.s0 = di.a0 == 0 ? 1 : (di.a0 == 1 ? g.nx : g.nx * g.ny);
+    ch.s1 = di.a1 == 0 ? 1 : (di.a1 == 1 ? g.nx : g.nx * g.ny);
+    ch.ds = di.ds;
+    ch.dc_hi = di.dcoef;
+    ch.dc_lo = di.dcoef_lo;
+    ch.src_amp = di.src_amp;
+    ch.m = 1;
+    ch.f = ch.T = ch.b0 = 0.0f;
+    if (kUniN) {
       int m;
       float f;
-      if (kUniN) {
-        m = m_s[k];
-        f = f_s[k];
-      } else {
-        retarded_delay(di.dcoef, di.dcoef_lo, nv_idx, m, f);
-      }
-      const int L0 = n - m, L1 = n - m - 1;
-      float Iup = 0.0f, Sup = 0.0f;
-      if (kind == 0) {
-        const int sd = dom == 0 ? 1 : (dom == 1 ? g.nx : g.nx * g.ny);
-        const int s0 = a0 == 0 ? 1 : (a0 == 1 ? g.nx : g.nx * g.ny);
-        const int s1 = a1 == 0 ? 1 : (a1 == 1 ? g.nx : g.nx * g.ny);
-        const size_t u = static_cast<size_t>(qd) * sd + static_cast<size_t>(q0) * s0 +
-                         static_cast<size_t>(q1) * s1;
-        float i0 = 0.0f, i1 = 0.0f, s0v = 0.0f, s1v = 0.0f;
-        if (L0 >= g.hist_from) {
-          i0 = __ldg(Iring + static_cast<size_t>(ring_slot(L0)) * ilevel + static_cast<size_t>(d) * plane + u);
-          s0v = __ldg(Sc0 + static_cast<size_t>(ring_slot(L0)) * slevel + u);
-        }
-        if (L1 >= g.hist_from) {
-          i1 = __ldg(Iring + static_cast<size_t>(ring_slot(L1)) * ilevel + static_cast<size_t>(d) * plane + u);
-          s1v = __ldg(Sc0 + static_cast<size_t>(ring_slot(L1)) * slevel + u);
-        }
-        Iup = (1.0f - f) * i0 + f * i1;
-        Sup = (1.0f - f) * s0v + f * s1v;
-      } else if (kind == 1 && static_cast<int>(v) == g.src_voxel && di.src_amp != 0.0f) {
-        const float on0 = (L0 >= 0 && L0 < g.pulse_steps) ? 1.0f : 0.0f;
-        const float on1 = (L1 >= 0 && L1 < g.pulse_steps) ? 1.0f : 0.0f;
-        Iup = di.src_amp * ((1.0f - f) * on0 + f * on1);
-      }
-      float T, b0;
-      if (kUniMu) {
-        T = T_s[k];
-        b0 = b0_s[k];
-      } else {
-        const float xo = mu * di.ds;
-        T = expf(-xo);
-        b0 = ray_b0(xo, T);
-      }
-      const float q = Iup * T + Sup * b0;
-      Qf[static_cast<size_t>(d) * plane + v] = q;
-      acc += q;
+      retarded_delay(di.dcoef, di.dcoef_lo, g.n_u, m, f);
+      ch.m = m < 1 ? 1 : (m > 3 ? 3 : m);
+      ch.f = f;
     }
-    Qc[static_cast<size_t>(c) * plane + v] = acc * inv;
+    if (kUniMu) {
+      const float xo = g.mut_u * di.ds;
+      const float T = expf(-xo);
+      ch.T = T;
+      ch.b0 = ray_b0(xo, T);
+    }
+    cs[k] = ch;
+  }
+  __syncthreads();
+  const int nrows = g.ny * g.nz;
+  const float inv = 1.0f / static_cast<float>(nch);
+  float* qc = Qc + static_cast<size_t>(c) * plane;
+
+  for (int row = blockIdx.x * blockDim.y + threadIdx.y; row < nrows; row += gridDim.x * blockDim.y) {
+    const int y = row % g.ny, z = row / g.ny;
+    for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
+      const int v = row * g.nx + x;
+      const float mu = kUniMu ? 0.0f : __ldg(mut + v);
+      const float nv_idx = kUniN ? 0.0f : __ldg(nidx + v);
+      float acc = 0.0f;
+      for (int k = 0; k < nch; ++k) {
+        const Child& ch = cs[k];
+        const int dom = ch.dom, sgn = ch.sgn, nd = ch.nd, n0 = ch.n0, n1 = ch.n1;
+        const int pd = pick(dom, x, y, z), p0 = pick(ch.a0, x, y, z), p1 = pick(ch.a1, x, y, z);
+        const int kp = sgn > 0 ? pd : nd - 1 - pd;
+        int qd = pd - sgn;
+        int q0 = p0 - ch.off0[kp];
+        int q1 = p1 - ch.off1[kp];
+        int kind = 0;
+        if (g.periodic) {
+          qd = (qd + nd) % nd;
+          q0 = (q0 + n0) % n0;
+          q1 = (q1 + n1) % n1;
+        } else if (kp == 0) {
+          kind = 1;
+        } else if (q0 < 0 || q0 >= n0 || q1 < 0 || q1 >= n1) {
+          kind = 2;
+        }
+        int m;
+        float f;
+        if (kUniN) {
+          m = ch.m;
+          f = ch.f;
+        } else {
+          retarded_delay(ch.dc_hi, ch.dc_lo, nv_idx, m, f);
+          m = m < 1 ? 1 : (m > 3 ? 3 : m);  // the optics check keeps every delay in [1, 4)
+        }
+        const int L0 = n - m, L1 = n - m - 1;
+        float Iup = 0.0f, Sup = 0.0f;
+        if (kind == 0) {
+          const int u = qd * ch.sd + q0 * ch.s0 + q1 * ch.s1;  // < nv <= 2^30
+          const float* i0p = ch.ilev[m];
+          const float* i1p = ch.ilev[m + 1];
+          float i0 = 0.0f, i1 = 0.0f, s0v = 0.0f, s1v = 0.0f;
+          if (i0p) {
+            i0 = __ldg(i0p + u);
+            s0v = __ldg(slev_s[m] + u);
+          }
+          if (i1p) {
+            i1 = __ldg(i1p + u);
+            s1v = __ldg(slev_s[m + 1] + u);
+          }
+          Iup = (1.0f - f) * i0 + f * i1;
+          Sup = (1.0f - f) * s0v + f * s1v;
+        } else if (kind == 1 && v == g.src_voxel && ch.src_amp != 0.0f) {
+          const float on0 = (L0 >= 0 && L0 < g.pulse_steps) ? 1.0f : 0.0f;
+          const float on1 = (L1 >= 0 && L1 < g.pulse_steps) ? 1.0f : 0.0f;
+          Iup = ch.src_amp * ((1.0f - f) * on0 + f * on1);
+        }
+        float T, b0;
+        if (kUniMu) {
+          T = ch.T;
+          b0 = ch.b0;
+        } else {
+          const float xo = mu * ch.ds;
+          T = expf(-xo);
+          b0 = ray_b0(xo, T);
+        }
+        const float q = Iup * T + Sup * b0;
+        ch.qf[v] = q;
+        acc += q;
+      }
+      qc[v] = acc * inv;
+    }
   }
 }
 
@@ -229,8 +263,9 @@ cudaError_t launch_sweep2(const GridParams& g, const DirInfo* dirs, const int8_t
   const int by = 256 / bx;
   const int rows = g.ny * g.nz;
   dim3 block(bx, by);
-  dim3 grid((rows + by - 1) / by, na_s);
-  const size_t smem = nch * sizeof(DirInfo);
+  const int groups = (rows + by - 1) / by;
+  dim3 grid((groups + kRowSweeps2 - 1) / kRowSweeps2, na_s);
+  const size_t smem = nch * sizeof(Child);
   const bool un = g.n_u >= 1.0f, um = g.mut_u >= 0.0f;
   if (un && um)
     sweep2_kernel<true, true><<<grid, block, smem, st>>>(g, dirs, offs, children, nch, na_s, Iring, Sring, mut,
