@@ -71,7 +71,8 @@ struct Tc {
   static constexpr int OFF_B1T = OFF_ALO + A_BYTES;                 // [kMaxClasses][kM] f32
   static constexpr int OFF_R = OFF_B1T + kMaxClasses * kM * 4;      // [NA] f32
   static constexpr int OFF_CLS = OFF_R + NA * 4;                    // [NA] u8 (padded)
-  static constexpr int OFF_END = OFF_CLS + ((NA + 15) / 16) * 16;
+  static constexpr int OFF_B1C = OFF_CLS + ((NA + 15) / 16) * 16;   // [NA] f32 (uniform mu_t)
+  static constexpr int OFF_END = OFF_B1C + NA * 4;
   static constexpr int SMEM = OFF_END + 1024;                       // + alignment slack
   static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
                                     (static_cast<uint32_t>(NA >> 3) << 17) |
@@ -289,7 +290,9 @@ __device__ __forceinline__ void load_b_operand(uint8_t* sB, const uint16_t* __re
 
 // ---------------------------------------------------------------- the iteration kernel
 
-template <int NA>
+// kUniB1: mu_t is the same in every voxel, so b1 depends on the column's ray spacing only
+// and is read per column (one vector load per chunk) instead of per class and row.
+template <int NA, bool kUniB1>
 __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
     scatter_tc_kernel(GridParams g, const float* __restrict__ rcorr, const uint8_t* __restrict__ cls,
                       const float* __restrict__ cls_ds, int ncls, int nch, const uint16_t* __restrict__ Pbf,
@@ -305,6 +308,7 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
   float* b1t = reinterpret_cast<float*>(smem + C::OFF_B1T);
   float* sR = reinterpret_cast<float*>(smem + C::OFF_R);
   uint8_t* sCls = smem + C::OFF_CLS;
+  float* sB1c = reinterpret_cast<float*>(smem + C::OFF_B1C);
 
   __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_base_s;
@@ -342,6 +346,15 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
   for (int i = tid; i < NA; i += blockDim.x) {
     sR[i] = rcorr[i];
     sCls[i] = cls[i];
+    if (kUniB1) {  // the same operations as the per-row table below, on the same mu_t
+      const int k = cls[i];
+      float bs = 0.0f;
+      for (int j = 0; j < nch; ++j) {
+        const float x = g.mut_u * cls_ds[k * nch + j];
+        bs += ray_b1(x, expf(-x));
+      }
+      sB1c[i] = bs * (1.0f / static_cast<float>(nch));
+    }
   }
   // zero the K padding of both A operands once (columns >= NA are never written again)
   if constexpr (C::KP > NA) {
@@ -389,7 +402,7 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
     }
     // a class is one spacing ds, or on a two-level angular grid the nch spacings of a
     // coarse direction's children (b1 is then their mean)
-    for (int u = tid; u < ncls * kM; u += blockDim.x) {
+    for (int u = tid; u < (kUniB1 ? 0 : ncls * kM); u += blockDim.x) {
       const int k = u / kM, r = u % kM;
       const int vv = brick_voxel(g, bxn, byn, tile, r);
       float bs = 0.0f;
@@ -419,8 +432,10 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
       for (int j = 0; j < C::CH; j += 2) {
         const float q0 = vin ? __ldg(Q + static_cast<size_t>(c0 + j) * plane + v) : 0.0f;
         const float q1 = vin ? __ldg(Q + static_cast<size_t>(c0 + j + 1) * plane + v) : 0.0f;
-        const float x0 = q0 + b1t[sCls[c0 + j] * kM + row] * so[j];
-        const float x1 = q1 + b1t[sCls[c0 + j + 1] * kM + row] * so[j + 1];
+        const float b1a = kUniB1 ? sB1c[c0 + j] : b1t[sCls[c0 + j] * kM + row];
+        const float b1b = kUniB1 ? sB1c[c0 + j + 1] : b1t[sCls[c0 + j + 1] * kM + row];
+        const float x0 = q0 + b1a * so[j];
+        const float x1 = q1 + b1b * so[j + 1];
         split_bf16x2(x0, x1, hi[j / 2], lo[j / 2]);
       }
       tmem_st<C::CH>(t_row + C::SOFF + c0, so);
@@ -476,17 +491,25 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
           tmem_ld<C::CH>(t_row + C::SOFF + c0, so);
           tmem_wait_ld();
           uint32_t hi[C::CH / 2], lo[C::CH / 2];
-          float rv[C::CH];
+          float rv[C::CH], bv[C::CH];
           uint32_t cv[C::CH / 4];
           lds_vec<C::CH>(sR + c0, rv);
-          lds_bytes<C::CH>(sCls + c0, cv);
+          if (kUniB1)
+            lds_vec<C::CH>(sB1c + c0, bv);
+          else
+            lds_bytes<C::CH>(sCls + c0, cv);
 #pragma unroll
           for (int j = 0; j < C::CH; j += 2) {
             float xn[2];
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
-              const int cl = static_cast<int>((cv[(j + e) >> 2] >> (8 * ((j + e) & 3))) & 0xffu);
-              const float b1 = vb1t[cl * kM + row];
+              float b1;
+              if (kUniB1) {
+                b1 = bv[j + e];
+              } else {
+                const int cl = static_cast<int>((cv[(j + e) >> 2] >> (8 * ((j + e) & 3))) & 0xffu);
+                b1 = vb1t[cl * kM + row];
+              }
               const float qv = q[ch * C::CH + j + e];
               const float xo = fmaf(b1, so[j + e], qv);              // X used by this iteration's MMA
               const float yc = fmaf(rv[j + e], xo, y[j + e]);        // D + r X
@@ -570,7 +593,9 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
 #pragma unroll
           for (int j = 0; j < C::CH; ++j) {
             if (mine) {
-              const float Iv = fmaf(vb1t[vCls[c0 + j] * kM + row], so[j], q[ch * C::CH + j]);
+              const float b1 = kUniB1 ? reinterpret_cast<const volatile float*>(sB1c)[c0 + j]
+                                      : vb1t[vCls[c0 + j] * kM + row];
+              const float Iv = fmaf(b1, so[j], q[ch * C::CH + j]);
               *pI = Iv;
               *pS = so[j];
               esum_row += Iv;
@@ -708,8 +733,10 @@ int g_num_sms = 0;
 
 template <int NA>
 cudaError_t configure() {
-  cudaError_t e = cudaFuncSetAttribute(scatter_tc_kernel<NA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(scatter_tc_kernel<NA, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        Tc<NA>::SMEM);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(scatter_tc_kernel<NA, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, Tc<NA>::SMEM);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(tc_tile_selftest_kernel<NA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               Tc<NA>::SMEM);
@@ -736,12 +763,21 @@ cudaError_t launch_scatter_bf16(const GridParams& g, const BfTables& t, const ui
                                 float* Sring, float tol, int max_iters, RunState rs, cudaStream_t st) {
   const int ntiles = brick_tiles(g.nx, g.ny, g.nz);
   const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
+  const bool uni = g.mut_u >= 0.0f;
   if (g.na == 48) {
-    scatter_tc_kernel<48><<<grid, Tc<48>::kThreads, Tc<48>::SMEM, st>>>(g, t.rcorr, t.cls, t.cls_ds, t.ncls, t.nch, Pbf, Q, mut,
-                                                                  eps, nidx, Iring, Sring, tol, max_iters, rs);
+    if (uni)
+      scatter_tc_kernel<48, true><<<grid, Tc<48>::kThreads, Tc<48>::SMEM, st>>>(
+          g, t.rcorr, t.cls, t.cls_ds, t.ncls, t.nch, Pbf, Q, mut, eps, nidx, Iring, Sring, tol, max_iters, rs);
+    else
+      scatter_tc_kernel<48, false><<<grid, Tc<48>::kThreads, Tc<48>::SMEM, st>>>(
+          g, t.rcorr, t.cls, t.cls_ds, t.ncls, t.nch, Pbf, Q, mut, eps, nidx, Iring, Sring, tol, max_iters, rs);
   } else if (g.na == 192) {
-    scatter_tc_kernel<192><<<grid, Tc<192>::kThreads, Tc<192>::SMEM, st>>>(g, t.rcorr, t.cls, t.cls_ds, t.ncls, t.nch, Pbf, Q,
-                                                                    mut, eps, nidx, Iring, Sring, tol, max_iters, rs);
+    if (uni)
+      scatter_tc_kernel<192, true><<<grid, Tc<192>::kThreads, Tc<192>::SMEM, st>>>(
+          g, t.rcorr, t.cls, t.cls_ds, t.ncls, t.nch, Pbf, Q, mut, eps, nidx, Iring, Sring, tol, max_iters, rs);
+    else
+      scatter_tc_kernel<192, false><<<grid, Tc<192>::kThreads, Tc<192>::SMEM, st>>>(
+          g, t.rcorr, t.cls, t.cls_ds, t.ncls, t.nch, Pbf, Q, mut, eps, nidx, Iring, Sring, tol, max_iters, rs);
   } else {
     return cudaErrorInvalidValue;
   }
