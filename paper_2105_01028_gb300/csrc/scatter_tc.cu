@@ -300,6 +300,10 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
                       const float* __restrict__ nidx, float* __restrict__ Iring, float* __restrict__ Sring,
                       float tol, int max_iters, RunState rs) {
   using C = Tc<NA>;
+  // TMEM load width: 16 columns where registers allow (the uniform-b1 form needs no class
+  // bytes), else 8
+  constexpr int CH = (kUniB1 && C::HALF % 16 == 0) ? 16 : C::CH;
+  constexpr int NCH = C::HALF / CH;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sB = smem + C::OFF_B;
@@ -421,15 +425,15 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
     // columns at a time (not unrolled) so that the chunk loads are not batched; Q is
     // re-read here and kept in registers only for the iteration loop below.
 #pragma unroll 1
-    for (int ch = 0; ch < C::NCH; ++ch) {
-      const int c0 = cb + ch * C::CH;
-      float so[C::CH];
-      uint32_t hi[C::CH / 2], lo[C::CH / 2];
+    for (int ch = 0; ch < NCH; ++ch) {
+      const int c0 = cb + ch * CH;
+      float so[CH];
+      uint32_t hi[CH / 2], lo[CH / 2];
 #pragma unroll
-      for (int j = 0; j < C::CH; ++j)
+      for (int j = 0; j < CH; ++j)
         so[j] = (vin && has_prev) ? Sring[prev_base + static_cast<size_t>(c0 + j) * plane + v] : 0.0f;
 #pragma unroll
-      for (int j = 0; j < C::CH; j += 2) {
+      for (int j = 0; j < CH; j += 2) {
         const float q0 = vin ? __ldg(Q + static_cast<size_t>(c0 + j) * plane + v) : 0.0f;
         const float q1 = vin ? __ldg(Q + static_cast<size_t>(c0 + j + 1) * plane + v) : 0.0f;
         const float b1a = kUniB1 ? sB1c[c0 + j] : b1t[sCls[c0 + j] * kM + row];
@@ -438,9 +442,9 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
         const float x1 = q1 + b1b * so[j + 1];
         split_bf16x2(x0, x1, hi[j / 2], lo[j / 2]);
       }
-      tmem_st<C::CH>(t_row + C::SOFF + c0, so);
+      tmem_st<CH>(t_row + C::SOFF + c0, so);
 #pragma unroll
-      for (int j = 0; j < C::CH; j += 8) {
+      for (int j = 0; j < CH; j += 8) {
         *reinterpret_cast<uint4*>(sAhi + sw128_chunk_off(kM, row, c0 + j)) =
             make_uint4(hi[j / 2], hi[j / 2 + 1], hi[j / 2 + 2], hi[j / 2 + 3]);
         *reinterpret_cast<uint4*>(sAlo + sw128_chunk_off(kM, row, c0 + j)) =
@@ -484,22 +488,22 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
       // lane; inactive lanes keep S_old (so they rewrite the same X) and report no change.
       if (!to && __any_sync(0xffffffffu, act)) {
 #pragma unroll
-        for (int ch = 0; ch < C::NCH; ++ch) {
-          const int c0 = cb + ch * C::CH;
-          float y[C::CH], so[C::CH];
-          tmem_ld<C::CH>(t_row + c0, y);
-          tmem_ld<C::CH>(t_row + C::SOFF + c0, so);
+        for (int ch = 0; ch < NCH; ++ch) {
+          const int c0 = cb + ch * CH;
+          float y[CH], so[CH];
+          tmem_ld<CH>(t_row + c0, y);
+          tmem_ld<CH>(t_row + C::SOFF + c0, so);
           tmem_wait_ld();
-          uint32_t hi[C::CH / 2], lo[C::CH / 2];
-          float rv[C::CH], bv[C::CH];
-          uint32_t cv[C::CH / 4];
-          lds_vec<C::CH>(sR + c0, rv);
+          uint32_t hi[CH / 2], lo[CH / 2];
+          float rv[CH], bv[CH];
+          uint32_t cv[CH / 4];
+          lds_vec<CH>(sR + c0, rv);
           if (kUniB1)
-            lds_vec<C::CH>(sB1c + c0, bv);
+            lds_vec<CH>(sB1c + c0, bv);
           else
-            lds_bytes<C::CH>(sCls + c0, cv);
+            lds_bytes<CH>(sCls + c0, cv);
 #pragma unroll
-          for (int j = 0; j < C::CH; j += 2) {
+          for (int j = 0; j < CH; j += 2) {
             float xn[2];
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
@@ -510,7 +514,7 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
                 const int cl = static_cast<int>((cv[(j + e) >> 2] >> (8 * ((j + e) & 3))) & 0xffu);
                 b1 = vb1t[cl * kM + row];
               }
-              const float qv = q[ch * C::CH + j + e];
+              const float qv = q[ch * CH + j + e];
               const float xo = fmaf(b1, so[j + e], qv);              // X used by this iteration's MMA
               const float yc = fmaf(rv[j + e], xo, y[j + e]);        // D + r X
               const float sn = act ? fmaf(-ev, yc, yc) : so[j + e];  // S_new = (1 - eps) Y
@@ -521,9 +525,9 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
             }
             split_bf16x2(xn[0], xn[1], hi[j / 2], lo[j / 2]);
           }
-          tmem_st<C::CH>(t_row + C::SOFF + c0, so);
+          tmem_st<CH>(t_row + C::SOFF + c0, so);
 #pragma unroll
-          for (int j = 0; j < C::CH; j += 8) {
+          for (int j = 0; j < CH; j += 8) {
             *reinterpret_cast<uint4*>(sAhi + sw128_chunk_off(kM, row, c0 + j)) =
                 make_uint4(hi[j / 2], hi[j / 2 + 1], hi[j / 2 + 2], hi[j / 2 + 3]);
             *reinterpret_cast<uint4*>(sAlo + sw128_chunk_off(kM, row, c0 + j)) =
@@ -585,17 +589,17 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
         float* pS = Sring + cur_base + static_cast<size_t>(cb) * pl + v;
         float esum_row = 0.0f;
 #pragma unroll
-        for (int ch = 0; ch < C::NCH; ++ch) {
-          const int c0 = cb + ch * C::CH;
-          float so[C::CH];
-          tmem_ld<C::CH>(t_row + C::SOFF + c0, so);
+        for (int ch = 0; ch < NCH; ++ch) {
+          const int c0 = cb + ch * CH;
+          float so[CH];
+          tmem_ld<CH>(t_row + C::SOFF + c0, so);
           tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < C::CH; ++j) {
+          for (int j = 0; j < CH; ++j) {
             if (mine) {
               const float b1 = kUniB1 ? reinterpret_cast<const volatile float*>(sB1c)[c0 + j]
                                       : vb1t[vCls[c0 + j] * kM + row];
-              const float Iv = fmaf(b1, so[j], q[ch * C::CH + j]);
+              const float Iv = fmaf(b1, so[j], q[ch * CH + j]);
               *pI = Iv;
               *pS = so[j];
               esum_row += Iv;
