@@ -24,8 +24,10 @@ for theta1 below the critical angle, R = 1 beyond it.
   normal incidence.
 
 Parity status: the optics (R, Snell direction, critical angle) are pinned against Eq. 14
-itself and textbook limits; the voxel-level redistribution has no closed form and rests
-on oracle-GPU agreement ("parity unpinned" beyond its conservation property).
+itself and textbook limits, and the whole redistribution table of a plane index step
+against directions and weights written out by hand; on curved interfaces the normal of a
+stair-stepped boundary has no closed form, and the redistribution there rests on
+oracle-GPU agreement ("parity unpinned" beyond its conservation property).
 """
 import numpy as np
 

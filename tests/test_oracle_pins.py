@@ -398,6 +398,60 @@ def test_snell_direction():
         assert np.sign(np.dot(om_t, m)) == np.sign(np.dot(om, m))
 
 
+def test_interface_redistribution_at_a_planar_step():
+    """A plane index step (n = 1.0 below z = 4, 1.4 from z = 4 up): every segment whose
+    upwind sample lies across the step is split into the mirror image of its direction
+    (weight R of Eq. 14 as printed) and the Snell direction written out by hand (weight
+    1 - R, none under total internal reflection), each snapped to the pixel with the
+    largest dot product by brute force (the reading's tie rule: lowest index within 1e-12);
+    no other segment is touched."""
+    nx, ny, nz, k0 = 6, 6, 8, 4
+    p = W.homogeneous(nx, ny, nz, 2, 0.01, 1.0, steps=1)
+    nmap = np.full((nz, ny, nx), 1.0)
+    nmap[k0:] = 1.4
+    p["nidx"] = nmap.astype(np.float32)
+    p["fresnel"] = True
+    m = Model(p)
+    n = m.nidx
+    expected = {}
+    for j in range(m.na):
+        up = m.lat.upwind_index(j)
+        for v in range(m.nv):
+            if up[v] < 0 or n[up[v]] == n[v]:
+                continue
+            n1, n2 = float(n[up[v]]), float(n[v])
+            ox, oy, oz = m.dirs[j]
+            cos1 = abs(oz)
+            th1 = math.acos(cos1)
+            eta = n1 / n2
+            sin2 = eta * eta * (1.0 - cos1 * cos1)
+            refl = np.array([ox, oy, -oz])
+            if sin2 >= 1.0:
+                R, trans = 1.0, None
+            else:
+                R = float(fresnel_R_eq14(n1, n2, th1))
+                trans = np.array([eta * ox, eta * oy, math.copysign(math.sqrt(1.0 - sin2), oz)])
+
+            def snap(vec):  # ties (mirror-symmetric pixel pairs) go to the lowest index
+                dots = m.dirs @ vec
+                return min(i for i in range(m.na) if dots[i] >= dots.max() - 1e-12)
+            outs = [(snap(refl), R)]
+            if trans is not None:
+                outs.append((snap(trans), 1.0 - R))
+            expected.setdefault(v, {})[j] = outs
+    assert expected and set(expected) == set(m.interfaces)
+    kinds = {len(outs) for cols in expected.values() for outs in cols.values()}
+    assert kinds == {1, 2}  # both total internal reflection and transmission occur
+    zs = {v // (nx * ny) for v in expected}
+    assert zs <= {k0 - 1, k0}
+    for v, cols in expected.items():
+        assert set(cols) == set(m.interfaces[v])
+        for j, outs in cols.items():
+            got = m.interfaces[v][j]
+            assert [d for d, _ in got] == [d for d, _ in outs]
+            np.testing.assert_allclose([w for _, w in got], [w for _, w in outs], rtol=0, atol=1e-12)
+
+
 def test_interface_redistribution_conserves_photons():
     """The interface operator is column-stochastic: the sum over directions of Q at every
     interface voxel is unchanged, and it moves intensity only where n changes."""
