@@ -22,11 +22,18 @@ fresnel    Snell's law (Eq. 13) and Fresnel reflectance (Eq. 14).
 solver     The time loop: ray update (Eqs. 9-10), source iteration (Eq. 12,
            §2.4 Steps 3, 5, 6, 7), boundary inflow and detectors (§3.1).
 bruteforce An independent per-ray tracer for tiny grids (cross-check of geometry).
+adjoint    Reverse-mode derivative of a detector misfit (checkpointed time loop).
+twolevel   Transport on fine directions, source function on coarse ones (§2.1).
+exact      Per-voxel source function from the fixed-point equation of Eq. 12.
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test in
-``tests/test_oracle_*.py`` except the Fresnel interface redistribution on voxel
-grids (``fresnel.interface_operator``), whose slab-level physics is pinned but whose
-full heterogeneous result is "parity unpinned".
+``tests/test_oracle_*.py`` except the Fresnel interface redistribution on curved
+interfaces (``fresnel.interface_operators``): its optics and its whole table on a plane
+index step are pinned, but on a stair-stepped curved boundary it is "parity unpinned".
+The adjoint (``adjoint``), the two-level angular grid (``twolevel``, with the HEALPix
+point location in ``healpix``) and the exact per-voxel solve (``exact``) are pinned in
+``tests/test_oracle_adjoint.py``, ``tests/test_oracle_twolevel.py`` and
+``tests/test_oracle_exact.py``.
 """
 
 C0_MM_PER_NS = 299.792458  # speed of light in vacuum, mm/ns (c = c0 / n, §2.1 below Eq. 1)
