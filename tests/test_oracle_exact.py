@@ -25,6 +25,22 @@ def test_operator_solves_the_fixed_point():
     assert not np.any(exact_operator(P, 0.0, b1))  # no scattering, no source
 
 
+def test_isotropic_scattering_has_a_closed_form():
+    """g = 0: every row of P is 1/N_a, so S is the same in every direction and the fixed
+    point reduces to the scalar S = a mean(Q) / (1 - a mean(b1)) (b1 still varies with the
+    ray spacing of each direction)."""
+    P = phase_matrix(2, 0.0)
+    np.testing.assert_allclose(P, np.full((48, 48), 1.0 / 48), rtol=1e-12)
+    rng = np.random.default_rng(1)
+    ds = 1.0 + 0.7 * rng.random(48)
+    for mut, a in ((10.0, 0.999), (1.0, 0.6)):
+        _, _, b1 = ray_weights(mut * ds)
+        Q = rng.random((48, 5))
+        S = exact_operator(P, a, b1) @ Q
+        closed = a * Q.mean(axis=0) / (1.0 - a * b1.mean())
+        np.testing.assert_allclose(S, np.broadcast_to(closed, S.shape), rtol=1e-11)
+
+
 def phantom(nside=2, steps=12, tol=1e-13):
     """10 x 10 x 8 voxels: background mu_a 0.02, mu_s 2 /mm, n 1.4; an absorbing sphere
     (mu_a x 4, radius 2 mm); an air block (mu_a = mu_s = 0, n 1) with interfaces."""
