@@ -21,13 +21,15 @@ cones      15-degree source / detector acceptance cones (§3.1).
 fresnel    Snell's law (Eq. 13) and Fresnel reflectance (Eq. 14).
 solver     The time loop: ray update (Eqs. 9-10), source iteration (Eq. 12,
            §2.4 Steps 3, 5, 6, 7), boundary inflow and detectors (§3.1).
-bruteforce An independent per-ray tracer for tiny grids (cross-check of geometry).
+bruteforce An independent per-ray tracer for tiny grids (cross-check of geometry);
+           it has its own dominant-axis and floor rules and imports nothing from here.
 adjoint    Reverse-mode derivative of a detector misfit (checkpointed time loop).
 twolevel   Transport on fine directions, source function on coarse ones (§2.1).
 exact      Per-voxel source function from the fixed-point equation of Eq. 12.
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test in
-``tests/test_oracle_*.py`` except the Fresnel interface redistribution on curved
+``tests/test_oracle_*.py`` (the detector tally, photon accounting, closed-box decay and
+mirror faces in ``tests/test_oracle_tallies.py``) except the Fresnel interface redistribution on curved
 interfaces (``fresnel.interface_operators``): its optics and its whole table on a plane
 index step are pinned, but on a stair-stepped curved boundary it is "parity unpinned".
 The adjoint (``adjoint``), the two-level angular grid (``twolevel``, with the HEALPix

@@ -130,6 +130,22 @@ class RayLattice:
         out = np.where(kprime == 0, -1, out)
         return out
 
+    def upwind_coords(self, d, voxels):
+        """Unwrapped (x, y, z) coordinates of the upwind sample of direction d for the given
+        flat voxel indices (each may lie one voxel outside the box on any axis)."""
+        nx, ny, nz = self.n_xyz
+        v = np.asarray(voxels, dtype=np.int64)
+        p = [v % nx, (v // nx) % ny, v // (nx * ny)]
+        n = [nx, ny, nz]
+        dom = int(self.dom[d])
+        sgn = int(self.sgn[d])
+        kprime = p[dom] if sgn > 0 else n[dom] - 1 - p[dom]
+        q = [c.copy() for c in p]
+        q[dom] = p[dom] - sgn
+        for j, a in enumerate(transverse_axes(dom)):
+            q[a] = p[a] - self.offsets[d][j][kprime]
+        return q
+
     def entry_face(self, d):
         """Face (0..5 = -x,+x,-y,+y,-z,+z) through which direction d enters at k' = 0."""
         dom = int(self.dom[d])

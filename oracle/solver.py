@@ -32,12 +32,28 @@ Per voxel v and direction d, at time level n (time step dt):
   the directions whose segment crosses an index step is split into the specular and
   Snell directions before the source iteration.
 * Boundaries: absorbing ("vacuum", §3.1: photons reaching the box boundary are lost,
-  nothing re-enters) or periodic (test configuration).  The pulse enters through the
-  face voxel of the source spot, for the directions of the source cone, during the
-  first ``pulse_steps`` levels; the ghost sample outside the face has S = 0.
+  nothing re-enters), periodic, or mirror (test configurations).  The pulse enters
+  through the face voxel of the source spot, for the directions of the source cone,
+  during the first ``pulse_steps`` levels; the ghost sample outside the face has S = 0.
+  Mirror (specular reflection at every face, read as the method of images): a ghost
+  upwind sample, at most one voxel outside on each axis, takes I and S of its image -
+  the voxel reached by reflecting it back across each face it lies beyond, which is the
+  nearest voxel inside - in the direction reflected in those faces (its components along
+  them negated), at the same retarded levels.
 * Detectors (§3.1): the outgoing flux through the face voxels of a disk, weighted per
   direction by the acceptance cone: E[k, bin(n)] += sum_v sum_d alpha_d Omega_cap
   (Omega_d . n_out) I(v, d) h^2 dt, with bin(n) = floor((n + 1/2) dt / bin_width).
+* Photon accounting, per step n (FP64): N(n) = h^3 / c0 sum_v n_v sum_d w I (the photon
+  energy of the samples: energy density I / c per unit solid angle, c = c0 / n, §2.1 under
+  Eq. 1); escaped(n) = sum over face voxels and outgoing d of w (Omega_d . n_out) I h^2 dt;
+  absorbed(n) = h^3 dt sum_v mu_a(v) sum_d w I (the absorption rate mu_a c times the
+  energy N, Eq. 1's mu_a term); injected(n) = the source's inflow through its face voxel
+  in step n; residual(n) = N(-1) + sum_{k<=n} [injected - escaped - absorbed](k) - N(n),
+  N(-1) the energy of the state before step 0.  The residual is the scheme's own photon
+  balance error, not a rounding check: it is zero once the light has left a box without
+  absorption, while a short pulse is in flight it oscillates because a sample sees the
+  pulse once per delay (a fraction of the steps), and in a closed box it follows the
+  discrete decay rate's departure from exp(-mu_a c t).
 """
 import numpy as np
 
@@ -50,6 +66,22 @@ from .fresnel import interface_operators, apply_interfaces
 
 SERIES_X = 1e-3  # below this optical depth the Eq. 9 weights use their Taylor series
 FLOOR = 1e-6     # absolute stop floor, relative to the grid-wide max |S| of the previous level
+
+
+def reflection_table(dirs):
+    """refl[d, mask]: the direction whose vector is Omega_d with the components of the axes
+    in ``mask`` (bit 0 = x, 1 = y, 2 = z) negated.  The HEALPix pixel set is symmetric under
+    each such reflection; a missing partner raises."""
+    na = dirs.shape[0]
+    out = np.empty((na, 8), dtype=np.int64)
+    for mask in range(8):
+        s = np.array([-1.0 if (mask >> a) & 1 else 1.0 for a in range(3)])
+        dots = (dirs * s[None, :]) @ dirs.T
+        best = np.argmax(dots, axis=1)
+        if np.any(dots[np.arange(na), best] < 1.0 - 1e-12):
+            raise ValueError("direction set is not symmetric under a face reflection")
+        out[:, mask] = best
+    return out
 
 
 def time_step(courant, h, n_ref):
@@ -157,8 +189,13 @@ class Model:
         # in the paper's fiducial runs); the transport grid unless a coarser one is named
         self.nside_s = int(prob.get("nside_scatter") or prob["nside"])
         self.P = phase_matrix(self.nside_s, float(prob["g"]))
-        self.periodic = prob.get("boundary", "vacuum") == "periodic"
+        self.boundary = prob.get("boundary", "vacuum")
+        if self.boundary not in ("vacuum", "periodic", "mirror"):
+            raise ValueError("unknown boundary %r" % self.boundary)
+        self.periodic = self.boundary == "periodic"
+        self.mirror = self.boundary == "mirror"
         self.lat = RayLattice(self.dirs, self.shape, self.h, self.periodic)
+        self.reflect = reflection_table(self.dirs) if self.mirror else None
         self.dt = time_step(prob["courant"], self.h, prob["n_ref"])
         mua = np.asarray(prob["mua"], dtype=np.float64).ravel()
         mus = np.asarray(prob["mus"], dtype=np.float64).ravel()
@@ -172,7 +209,7 @@ class Model:
         # source inflow
         self.src = None
         src = prob.get("source")
-        if src is not None and not self.periodic:
+        if src is not None and self.boundary == "vacuum":
             face = int(src["face"])
             iu, iv = face_spot(self.shape, self.h, face, src["u_mm"], src["v_mm"])
             amp = src.get("amp")
@@ -201,7 +238,7 @@ class Model:
 
         # face outflow for the escaped-energy tally
         self.faces = []
-        if not self.periodic:
+        if self.boundary == "vacuum":
             for face in range(6):
                 ax, sign, (ua, va) = face_axes(face)
                 n = (nx, ny, nz)
@@ -221,7 +258,27 @@ class Model:
         f = delta - m
         x = self.mut[None, vox] * self.lat.ds[:, None]
         T, b0, b1 = ray_weights(x)
-        return dict(vox=vox, up=up, m=m, f=f, T=T, b0=b0, b1=b1)
+        seg = dict(vox=vox, up=up, m=m, f=f, T=T, b0=b0, b1=b1)
+        if self.mirror:
+            # image of each ghost upwind sample and the reflected direction it is read in
+            nx, ny, nz = self.shape[2], self.shape[1], self.shape[0]
+            n = (nx, ny, nz)
+            img = np.full(up.shape, -1, dtype=np.int64)
+            dstar = np.tile(np.arange(self.na)[:, None], (1, vox.size))
+            for d in range(self.na):
+                ghost = up[d] < 0
+                if not np.any(ghost):
+                    continue
+                q = self.lat.upwind_coords(d, vox[ghost])
+                mask = np.zeros(q[0].shape, dtype=np.int64)
+                for a in range(3):
+                    out = (q[a] < 0) | (q[a] >= n[a])
+                    mask |= out.astype(np.int64) << a
+                    q[a] = np.clip(q[a], 0, n[a] - 1)
+                img[d, ghost] = (q[2] * ny + q[1]) * nx + q[0]
+                dstar[d, ghost] = self.reflect[d, mask]
+            seg["img"], seg["dstar"] = img, dstar
+        return seg
 
     def inflow(self, seg, level):
         """Inflow intensity at time ``level`` for the (d, v) pairs with up == -1."""
@@ -246,6 +303,9 @@ def _retarded(hist, seg, n, which, model):
         v = np.zeros(up.shape)
         ok = (up >= 0) & (lev >= -(RING_DEPTH - 1))
         v[ok] = hist(which, lev[ok], dd[ok], up[ok])
+        if "img" in seg:  # mirror faces: the image sample in the reflected direction
+            im = (up < 0) & (lev >= -(RING_DEPTH - 1))
+            v[im] = hist(which, lev[im], seg["dstar"][im], seg["img"][im])
         if which == "I":
             v = v + model.inflow(seg, lev)
         vals.append(v)
@@ -299,6 +359,15 @@ class Solver:
         self.det = np.zeros((len(m.dets), m.nbins))
         self.energy = []
         self.escaped = []
+        self.absorbed = []
+        self.injected = []
+        self.residual = []
+        # energy of the state before step 0 (the held initial level, else nothing)
+        self.energy_init = 0.0
+        if init is not None:
+            I0 = np.broadcast_to(np.asarray(init[0], dtype=np.float64), (m.na, m.nv))
+            self.energy_init = m.h**3 / C0_MM_PER_NS * np.sum(m.nidx[None, :] * m.w * I0)
+        self._balance = self.energy_init
         self.iters_max = []
         self.iters_mean = []
 
@@ -333,11 +402,18 @@ class Solver:
         for k, det in enumerate(m.dets):
             if b < m.nbins:
                 self.det[k, b] += h2dt * np.sum(det["weight"][:, None] * I[:, det["voxels"]])
-        self.energy.append(m.h**3 / C0_MM_PER_NS * np.sum(m.nidx[None, :] * m.w * I))
+        N = m.h**3 / C0_MM_PER_NS * np.sum(m.nidx[None, :] * m.w * I)
+        self.energy.append(N)
         esc = 0.0
         for vox, cos_out in m.faces:
             esc += m.w * h2dt * np.sum(cos_out[:, None] * I[:, vox])
         self.escaped.append(esc)
+        ab = m.h**3 * m.dt * m.w * np.sum(m.mua[None, :] * I)
+        self.absorbed.append(ab)
+        inj = injected_energy(m, n)
+        self.injected.append(inj)
+        self._balance += inj - esc - ab
+        self.residual.append(self._balance - N)
 
     def run(self, nsteps):
         for _ in range(nsteps):
@@ -346,7 +422,9 @@ class Solver:
 
     def result(self):
         return dict(detectors=self.det.copy(), energy=np.array(self.energy),
-                    escaped=np.array(self.escaped), iters_max=np.array(self.iters_max),
+                    escaped=np.array(self.escaped), absorbed=np.array(self.absorbed),
+                    injected=np.array(self.injected), residual=np.array(self.residual),
+                    iters_max=np.array(self.iters_max),
                     iters_mean=np.array(self.iters_mean), steps=self.n)
 
     def level(self, which, back=0):
@@ -356,6 +434,22 @@ class Solver:
         if lev < 0:
             return np.zeros(arr.shape[1:])
         return arr[lev % RING_DEPTH].copy()
+
+
+def injected_energy(model, n):
+    """Energy the source's inflow carries into the box during step n: the ghost sample's
+    intensity at level n times w |Omega_d . n| h^2 dt, summed over the source directions."""
+    src = model.src
+    if src is None or not (0 <= n < src["pulse_steps"]):
+        return 0.0
+    ax, _, _ = face_axes(src["face"])
+    return float(np.sum(src["amp"] * model.w * np.abs(model.dirs[:, ax])) * model.h**2 * model.dt)
+
+
+def energy_density(model, I):
+    """Photon energy density per voxel, u = (n / c0) sum_d w I_d (§3.1 plots its maps; the
+    energy density of radiance I per unit solid angle is I / c, c = c0 / n)."""
+    return model.nidx / C0_MM_PER_NS * model.w * np.sum(I, axis=0)
 
 
 def one_step_at(model, n, hist, voxels, s_glob):
