@@ -14,8 +14,11 @@ Keys beyond the base contract: "roofline" (the dominant kernel against the measu
 peak), "kernels" (all kernels), "cpu_baseline" (the FP64 oracle timed on the host on a
 bounded voxel sample), "e2e" (the whole job through the public API from host buffers),
 "clocks" (nvidia-smi samples during the timed window), "iterations" (source-iteration
-statistics of the window), "fp32" (the plain-FP32 path on the same window, when the
-headline precision is BF16).
+statistics of the window), and one object per other measured workload, each with its
+own time per step, roofline and clocks: "fp32" (the plain-FP32 path on the same slab and
+window), "config1" (16^3 voxels, 48 directions, 100 graph-replayed steps, plain FP32 and
+BF16-scatter), "config3" (the 128 x 128 x 96 heterogeneous phantom with Fresnel
+interfaces, BF16 scatter and FP32 sweep, on the general per-voxel kernel forms).
 
 --impl reference times the oracle alone (see CpuLeg) on the same workload.
 """
@@ -38,8 +41,18 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
                   "sm_max_mhz": 2070.0}
 METRIC = "cell*dir*step updates/s"
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
+
+
+def sm_count():
+    """Streaming multiprocessors of the device the bench runs on (queried, not assumed)."""
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+
+
+def fp32_peak_tflops(pk):
+    """FP32 FFMA peak: SMs x 128 FP32 lanes x 2 FLOP x the measured maximum SM clock."""
+    return sm_count() * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
 
 
 def peaks():
@@ -166,7 +179,7 @@ def run_reference(args):
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * info["seconds"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args),
+            "config": workload_config(args, precision="fp64 (oracle)"),
             "cpu_baseline": {"value": value, "unit": "updates/s", "cores": cpu_cores(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0,
@@ -224,7 +237,9 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def workload_config(args):
+def workload_config(args, precision=None):
+    """The headline workload's description; ``precision`` names the arithmetic of the arm
+    that reports it (the reference arm: the FP64 oracle)."""
     nx, ny, nz = args.grid
     if args.two_level:
         dirs = "3072 HEALPix transport dirs (Nside 16), source function on 192 (Nside 4, mean of 16 children)"
@@ -239,59 +254,86 @@ def workload_config(args):
                 args.spinup + args.warmup, args.spinup + args.warmup + args.steps - 1),
             "tol": 1e-6, "l2": "inputs larger than L2 (%s time-level history per solve)" % hist,
             "parallelism": "replicas" if dist_env()[0] > 1 else "single GPU",
-            "precision": args.precision,
+            "precision": precision or ("fp32" if args.exact else args.precision),
             "source_function": "exact per-voxel solve S = M Q" if args.exact else "source iteration (Eq. 12)"}
 
 
 def run_serve(args):
-    """Served stream (a bounded sample of the served workload): Poisson arrivals, cubic
-    grids drawn from 32..64 voxels (the full stream draws 32..96), 48 or 192 directions,
-    100..300 steps (the full stream draws 500..1500), log-normal random-field optics.
-    Requests are submitted at their arrival times; reports solves/s over the makespan,
-    p50/p99 latency (submission to detector curves on the host), aggregate updates/s
-    and the largest number of concurrent solves."""
+    """Served stream (the served workload, a bounded number of requests): cubic grids of
+    32..96 voxels, 48 or 192 directions, 500..1500 steps, log-normal random-field optics
+    (workloads.served_stream / config_served).  First the capacity is measured: a burst of
+    --serve-burst requests submitted at once, solves/s over its makespan.  Then for each
+    rate factor in --rates a stream of --serve requests arrives as a Poisson process at
+    that fraction of the capacity, each request submitted at its arrival time; reported
+    per rate: solves/s over the makespan, p50/p99 latency (submission to detector curves on
+    the host), aggregate updates/s and the largest number of concurrent solves."""
     import torch
     import paper_2105_01028_gb300 as T
     torch.cuda.set_device(0)
-    rng = np.random.default_rng(4)
-    reqs = []
-    t = 0.0
-    for k in range(args.serve):
-        t += rng.exponential(1.0 / args.rate)
-        n = int(rng.integers(32, 65))
-        ns = 2 if rng.random() < 0.5 else 4
-        steps = int(rng.integers(100, 301))
-        reqs.append((t, W.config_served(n, ns, steps, seed=1000 + k, precision=args.precision)))
+
+    def draw(n_req, seed, rate):
+        out = []
+        for k, r in enumerate(W.served_stream(n_req, seed=seed, rate_per_s=rate)):
+            p = W.config_served(r["n"], r["nside"], r["steps"], seed=r["seed"], precision=args.precision)
+            p["steps"] = r["steps"]
+            out.append((r["arrival_s"], p))
+        return out
+
+    def updates(reqs):
+        return sum(p["nx"] * p["ny"] * p["nz"] * 12 * p["nside"] ** 2 * p["steps"] for _, p in reqs)
+
     free, total = torch.cuda.mem_get_info()
     srv = T.Server(hbm_budget_bytes=int(0.8 * free), max_slots=args.slots, steps_per_slice=32)
-    # warm-up: one small request (first-use costs of the library and the device)
     wid = srv.submit(W.config_served(16, 2, 10, seed=1, precision=args.precision))
     srv.wait(wid)
-    ids = []
-    t0 = time.perf_counter()
-    for at, p in reqs:
-        dt = at - (time.perf_counter() - t0)
-        if dt > 0:
-            time.sleep(dt)
-        ids.append(srv.submit(p))
-    lat = []
-    for rid in ids:
-        st, rc, det, ms = srv.wait(rid, timeout_s=3600)
-        if st != T.REQ_DONE:
-            raise RuntimeError("request %d ended in state %d (status %d)" % (rid, st, rc))
-        lat.append(ms)
-    span = time.perf_counter() - t0
-    updates = sum(p["nx"] * p["ny"] * p["nz"] * 12 * p["nside"] ** 2 * p["steps"] for _, p in reqs)
+
+    def play(reqs, timed_arrivals):
+        ids = []
+        t0 = time.perf_counter()
+        for at, p in reqs:
+            if timed_arrivals:
+                dt = at - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+            ids.append(srv.submit(p))
+        lat = []
+        for rid in ids:
+            st, rc, det, ms = srv.wait(rid, timeout_s=7200)
+            if st != T.REQ_DONE:
+                raise RuntimeError("request %d ended in state %d (status %d)" % (rid, st, rc))
+            lat.append(ms)
+        return time.perf_counter() - t0, np.array(lat)
+
+    burst = draw(args.serve_burst, 40, 1.0)
+    span, blat = play(burst, False)
+    capacity = len(burst) / span
+    c0 = srv.stats()["max_concurrent"]
+    results = []
+    for f in args.rates:
+        reqs = draw(args.serve, 4, f * capacity)
+        span, lat = play(reqs, True)
+        st = srv.stats()
+        results.append({"rate_factor": f, "arrival_rate_per_s": f * capacity, "requests": len(reqs),
+                        "solves_per_s": len(reqs) / span, "makespan_s": span,
+                        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                                       "max": float(np.max(lat))},
+                        "updates_per_s": updates(reqs) / span, "max_concurrent_so_far": st["max_concurrent"]})
     stats = srv.stats()
     srv.close()
-    line = {"metric": "served solves/s", "value": len(reqs) / span, "unit": "solves/s", "n_gpus": 1,
+    head = results[-1]
+    line = {"metric": "served solves/s", "value": head["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
             "higher_is_better": True, "precision": args.precision, "data": "synthetic",
-            "config": {"workload": "served stream sample: %d requests, Poisson arrivals at %.1f/s, cubic "
-                                   "32..64 voxels, 48/192 dirs, 100..300 steps, log-normal GRF optics"
-                                   % (len(reqs), args.rate), "slots": args.slots},
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "max": float(np.max(lat))},
-            "updates_per_s": updates / span, "makespan_s": span,
+            "config": {"workload": "served stream: cubic 32..96 voxels @1mm, 48/192 dirs (p = 1/2), 500..1500 "
+                                   "steps, log-normal GRF optics (sigma 0.3, correlation 5 mm, median mu_a "
+                                   "0.01/mm, mu_s 10/mm), g 0.9, n 1.4; Poisson arrivals at the stated "
+                                   "fractions of the measured capacity; %d requests per rate (bounded "
+                                   "sample of the 2000-request stream)" % args.serve,
+                       "slots": args.slots, "steps_per_slice": 32},
+            "capacity": {"solves_per_s": capacity, "burst_requests": len(burst), "makespan_s": len(burst) / capacity,
+                         "updates_per_s": updates(burst) * capacity / len(burst), "max_concurrent": c0,
+                         "burst_latency_ms": {"p50": float(np.percentile(blat, 50)),
+                                              "p99": float(np.percentile(blat, 99))}},
+            "rates": results, "latency_ms": head["latency_ms"],
             "max_concurrent": stats["max_concurrent"], "completed": stats["completed"]}
     print(json.dumps(line))
 
@@ -366,7 +408,7 @@ def run_adjoint(args):
     ad = float(np.sum(ga * (p["mua"] * da).ravel()) + np.sum(gs * (p["mus"] * ds).ravel()))
 
     pk = peaks()
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    fp32_peak = fp32_peak_tflops(pk)
     hbm = pk["hbm_gbs"]
     upd = nv * na * steps
     it_adj = float(st[6])
@@ -409,7 +451,7 @@ def run_adjoint(args):
             "roofline": {"kernel": "adj_scatter_fp32", "bound": "alu", "achieved": solve_ach,
                          "peak": fp32_peak, "unit": "TFLOP/s", "frac": solve_ach / fp32_peak,
                          "traffic": measured_traffic("adj_scatter_fp32_kernel", nv * na),
-                         "peak_source": "FP32 FFMA: 152 SMs x 128 lanes x 2 x max SM clock"},
+                         "peak_source": "FP32 FFMA: %d SMs x 128 lanes x 2 x max SM clock" % sm_count()},
             "phases": phases,
             "forward_scatter_tflops": fwd_flops / (ms_fwd * 1e-3) / 1e12,
             "misfit": L, "grad_max": {"mua": float(np.abs(ga).max()), "mus": float(np.abs(gs).max())},
@@ -425,6 +467,114 @@ def run_adjoint(args):
     print(json.dumps(line))
 
 
+def kernel_roofline(nv, na, na_s, kms, kp, k_mean, precision, pk, exact=False):
+    """Per-kernel times (ms per step) and the roofline object of the dominant kernel from
+    ``kp`` profiled steps (``kms``: summed ms of sweep, source function, tallies)."""
+    hbm = pk["hbm_gbs"]
+    sweep_bytes = nv * na * 20 + nv * 8  # I,S at two levels read (16 B), Q written (4 B); optics
+    scat_bytes = nv * na_s * 16 + nv * 12  # Q, S(n-1) read, I, S written; optics
+    scat_flops = 2.0 * na_s * na_s * nv * (1.0 if exact else k_mean)
+    per = [kms[0] / kp, kms[1] / kp, kms[2] / kp]
+    tot = sum(per)
+    if precision == "bf16" and not exact:
+        s_bound, s_peak = "tensor", pk.get("bf16_tflops_sustained", 1700.0)
+    else:
+        s_bound, s_peak = "alu", fp32_peak_tflops(pk)
+    s_ach = scat_flops / (per[1] * 1e-3) / 1e12
+    w_ach = sweep_bytes / (per[0] * 1e-3) / 1e9
+    kernels = [
+        {"name": "sweep", "ms": per[0], "share": per[0] / tot, "bound": "hbm", "achieved": w_ach,
+         "peak": hbm, "unit": "GB/s", "frac": w_ach / hbm, "algorithmic_bytes": sweep_bytes},
+        {"name": "exact_fp32" if exact else "scatter_" + precision, "ms": per[1], "share": per[1] / tot,
+         "bound": s_bound, "achieved": s_ach, "peak": s_peak, "unit": "TFLOP/s", "frac": s_ach / s_peak,
+         "algorithmic_flops": scat_flops, "hbm_gbs": scat_bytes / (per[1] * 1e-3) / 1e9},
+        {"name": "tally+advance", "ms": per[2], "share": per[2] / tot},
+    ]
+    dom = max(kernels[:2], key=lambda k: k["ms"])
+    roof = {"kernel": dom["name"], "bound": dom["bound"], "achieved": dom["achieved"], "peak": dom["peak"],
+            "unit": dom["unit"], "frac": dom["frac"], "traffic": None,
+            "peak_source": pk["_source"] + (" (FP32 FFMA: %d SMs x 128 lanes x 2 x max SM clock)" % sm_count()
+                                            if dom["bound"] == "alu" else "")}
+    return kernels, roof
+
+
+def measure_window(T, torch, prob, stream, spinup, warmup, steps, what):
+    """One more workload for the bench line: spin the solve up for ``spinup`` steps, run
+    ``warmup`` more, then time ``steps`` graph-replayed steps with CUDA events on the
+    library's stream (clocks sampled meanwhile), and time up to 10 further steps kernel
+    by kernel.  Returns its sub-object."""
+    fwd = T.Forward(prob, stream=stream.cuda_stream)
+    fwd.run(spinup + warmup)
+    fwd.sync()
+    first = fwd.steps_done()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        ev0.record(stream)
+        fwd.run(steps)
+        ev1.record(stream)
+        stream.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    status = fwd.sync()
+    it_max, it_mean = fwd.iterations()
+    kp = min(steps, 10)
+    kms = fwd.profile(kp)
+    _, k_it_mean = fwd.iterations()
+    executed = fwd.executed_iterations()[first:first + steps]
+    fwd.close()
+    nv = prob["nx"] * prob["ny"] * prob["nz"]
+    na = 12 * prob["nside"] ** 2
+    prec = prob.get("precision", "fp32")
+    kernels, roof = kernel_roofline(nv, na, na, kms, kp, float(np.mean(k_it_mean[-kp:])), prec, peaks())
+    return {"workload": what, "precision": prec, "value": nv * na * steps / (ms * 1e-3), "unit": "updates/s",
+            "ms_per_step": ms / steps, "window": "time steps %d..%d" % (first, first + steps - 1),
+            "iterations": {"mean": float(np.mean(it_mean[first:first + steps])),
+                           "max": int(np.max(it_max[first:first + steps])),
+                           "executed_per_voxel": float(np.mean(executed))},
+            "status": int(status), "gpu_launches": 4 * steps, "roofline": roof, "kernels": kernels,
+            "clocks": clk.summary()}
+
+
+def measure_whole_run(T, torch, prob, stream, steps, what, repeats=5):
+    """A short solve timed whole, from step 0 (context set up and warmed beforehand): the
+    best of ``repeats`` runs of ``steps`` graph-replayed steps after a reset."""
+    fwd = T.Forward(prob, stream=stream.cuda_stream)
+    fwd.run(steps)  # first use: graph capture, module load
+    fwd.sync()
+    best = None
+    with ClockSampler(0) as clk:
+        for _ in range(repeats):
+            fwd.reset()
+            torch.cuda.synchronize()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            fwd.run(steps)
+            ev1.record(stream)
+            stream.synchronize()
+            ms = ev0.elapsed_time(ev1)
+            best = ms if best is None else min(best, ms)
+    status = fwd.sync()
+    it_max, it_mean = fwd.iterations()
+    fwd.reset()
+    kms = fwd.profile(steps)
+    _, k_it_mean = fwd.iterations()
+    fwd.close()
+    nv = prob["nx"] * prob["ny"] * prob["nz"]
+    na = 12 * prob["nside"] ** 2
+    prec = prob.get("precision", "fp32")
+    kernels, roof = kernel_roofline(nv, na, na, kms, steps, float(np.mean(k_it_mean)), prec, peaks())
+    return {"workload": what, "precision": prec, "value": nv * na * steps / (best * 1e-3), "unit": "updates/s",
+            "ms_per_step": best / steps, "steps": steps,
+            "timing": "whole %d-step solve from step 0, best of %d (CUDA events; graph replay)" % (steps, repeats),
+            "iterations": {"mean": float(np.mean(it_mean)), "max": int(np.max(it_max))},
+            "status": int(status), "gpu_launches": 4 * steps, "roofline": roof, "kernels": kernels,
+            "clocks": clk.summary(),
+            "l2": "L2-resident (%.1f MB of time-level history): launch- and latency-bound" % (
+                2 * 5 * nv * na * 4 / 1e6)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -433,8 +583,10 @@ def main():
     ap.add_argument("--spinup", type=int, default=600)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
-    ap.add_argument("--compare-fp32", action="store_true",
-                    help="also time the plain FP32 path on the same window")
+    ap.add_argument("--no-fp32", action="store_true",
+                    help="skip the plain-FP32 slab on the same window (timed by default)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 16^3 and heterogeneous-phantom workloads (timed by default)")
     ap.add_argument("--cpu-voxels", type=int, default=16384,
                     help="voxels in the CPU-baseline sample of this arm (about 10 s of oracle work)")
     ap.add_argument("--ref-voxels", type=int, default=2048,
@@ -443,8 +595,11 @@ def main():
     ap.add_argument("--grid", type=int, nargs=3, default=[96, 96, 64], metavar=("NX", "NY", "NZ"),
                     help="slab size (smaller grids are for profiling captures only)")
     ap.add_argument("--serve", type=int, default=0, metavar="N",
-                    help="run the served stream with N requests instead of the slab")
-    ap.add_argument("--rate", type=float, default=8.0, help="served stream arrival rate (1/s)")
+                    help="run the served stream with N requests per rate instead of the slab")
+    ap.add_argument("--serve-burst", type=int, default=12,
+                    help="requests of the capacity measurement (submitted at once)")
+    ap.add_argument("--rates", type=float, nargs="+", default=[0.5, 0.8, 1.0],
+                    help="arrival rates as fractions of the measured capacity")
     ap.add_argument("--slots", type=int, default=8, help="served stream concurrent slots")
     ap.add_argument("--exact", action="store_true",
                     help="exact per-voxel source function (one optics class on the slab) instead of the iteration")
@@ -543,7 +698,7 @@ def main():
     scat_flops = 2.0 * na_s * na_s * nv * k_mean  # angular sum per voxel per iteration
     per = [kms[0] / kp, kms[1] / kp, kms[2] / kp]
     tot = sum(per)
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    fp32_peak = fp32_peak_tflops(pk)
     if args.precision == "bf16" and not args.exact:
         s_bound, s_peak, s_unit = "tensor", pk.get("bf16_tflops_sustained", 1700.0), "TFLOP/s"
     else:
@@ -574,7 +729,7 @@ def main():
                else measured_traffic("sweep2_kernel" if nch > 1 else "sweep_kernel", nv * na))
     roof = {"kernel": dom["name"], "bound": dom["bound"], "achieved": dom["achieved"],
             "peak": dom["peak"], "unit": dom["unit"], "frac": dom["frac"], "traffic": traffic,
-            "peak_source": pk["_source"] + (" (FP32 FFMA: 152 SMs x 128 lanes x 2 x max SM clock)"
+            "peak_source": pk["_source"] + (" (FP32 FFMA: %d SMs x 128 lanes x 2 x max SM clock)" % sm_count()
                                             if dom["bound"] == "alu" else "")}
 
     line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": ws,
@@ -593,20 +748,29 @@ def main():
                     "h2d_bytes_per_step": 3 * nv * 4 / job_steps,
                     "d2h_bytes_per_step": (det.size * 8 + N.size * 16) / job_steps}}
 
-    if args.compare_fp32 and args.precision != "fp32":
+    plain = not (args.two_level or args.exact)
+    if plain and args.precision != "fp32" and not args.no_fp32:
         p32 = W.config_slab(steps=total, precision="fp32", nx=nx, ny=ny, nz=nz)
-        f32 = T.Forward(p32, stream=stream.cuda_stream)
-        f32.run(args.spinup + args.warmup)
-        f32.sync()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        f32.run(args.steps)
-        e1.record(stream)
-        stream.synchronize()
-        m32 = e0.elapsed_time(e1)
-        line["fp32"] = {"value": ws * updates / (m32 * 1e-3), "ms_per_step": m32 / args.steps}
-        f32.close()
+        sub = measure_window(T, torch, p32, stream, args.spinup, args.warmup, args.steps,
+                             "the same slab and time window, plain FP32 (source iteration on CUDA cores)")
+        sub["value"] *= ws
+        sub["bf16_speedup"] = line["value"] / sub["value"]
+        line["fp32"] = sub
+    if plain and not args.no_configs and args.grid == [96, 96, 64]:
+        c1 = {}
+        for prec in ("fp32", "bf16"):
+            p1 = W.config_small(steps=100, precision=prec)
+            c1[prec] = measure_whole_run(T, torch, p1, stream, 100,
+                                         "16^3 voxels @1mm, 48 HEALPix dirs (Nside 2), mu_a 0.01/mm, "
+                                         "mu_s 10/mm, g 0.9, n 1.4, 15-deg pulse, 4 detectors, 100 steps, "
+                                         "tol 1e-6")
+        line["config1"] = c1
+        p3 = W.config_hetero(steps=args.spinup + args.warmup + args.steps + 16, precision="bf16")
+        line["config3"] = measure_window(
+            T, torch, p3, stream, args.spinup, args.warmup, args.steps,
+            "heterogeneous phantom 128x128x96 @1mm, 192 dirs, slab optics, air cylinder r 5 mm (n 1) with "
+            "Fresnel refraction/reflection at its wall, 3 absorbing spheres r 4/6/8 mm (mu_a x2/x3.5/x5), "
+            "-x face pulse, 8 detectors; BF16 scatter, FP32 sweep, general per-voxel kernel forms")
 
     if args.two_level or args.exact:
         line["cpu_baseline"] = None

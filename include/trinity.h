@@ -50,9 +50,9 @@ typedef enum {
   TRINITY_E_UNSUPPORTED = -6   /* the device cannot run this (e.g. not sm_103) */
 } trinity_status;
 
-enum { TRINITY_BOUNDARY_VACUUM = 0, TRINITY_BOUNDARY_PERIODIC = 1 };
+enum { TRINITY_BOUNDARY_VACUUM = 0, TRINITY_BOUNDARY_PERIODIC = 1, TRINITY_BOUNDARY_MIRROR = 2 };
 enum { TRINITY_FP32 = 0, TRINITY_BF16 = 1 };
-enum { TRINITY_FIELD_I = 0, TRINITY_FIELD_S = 1 };
+enum { TRINITY_FIELD_I = 0, TRINITY_FIELD_S = 1, TRINITY_FIELD_U = 2 };
 
 /*
  * Grid and solver description.
@@ -63,7 +63,14 @@ enum { TRINITY_FIELD_I = 0, TRINITY_FIELD_S = 1 };
  *                (the paper's rule "dt = fraction x light-crossing time of a grid",
  *                Sections 2.2 and 3.1).
  *   n_ref        refractive index used to define dt.
- *   boundary     TRINITY_BOUNDARY_VACUUM (absorbing faces, Section 3.1) or _PERIODIC.
+ *   boundary     TRINITY_BOUNDARY_VACUUM (absorbing faces, Section 3.1), _PERIODIC, or
+ *                _MIRROR (test configuration: every face reflects specularly, by the
+ *                method of images: a ray sample whose upwind sample lies outside the box
+ *                takes I and S of that sample's image - the nearest voxel inside - in the
+ *                direction reflected in the faces it lay beyond, at its own retarded
+ *                levels).  Periodic and mirror boxes take no source and count no escape;
+ *                mirror is not available on a two-level grid or for the adjoint
+ *                (TRINITY_E_UNSUPPORTED).
  *   precision    TRINITY_FP32 (all arithmetic FP32) or TRINITY_BF16 (the angular
  *                scattering sum of Eq. 12 in BF16 with FP32 accumulation on the tensor
  *                cores; transport FP32; detector and energy sums FP64 in both modes).
@@ -186,10 +193,22 @@ int trinity_sync(trinity_ctx* ctx);
 /* Detector curves, FP64 [n_det][nbins] (n must equal n_det * nbins). */
 int trinity_read_detectors(trinity_ctx* ctx, double* out, size_t n);
 
-/* Per-step tallies of the last ``nsteps`` completed steps (FP64): photon energy in the box
- * N(t) = sum_v h^3 n_v / c0 sum_d w I, and energy escaped through all faces in the step.
- * Either pointer may be NULL. */
-int trinity_read_energy(trinity_ctx* ctx, double* N_t, double* escaped, size_t nsteps);
+/* Per-step photon accounting of the last ``nsteps`` completed steps, each [nsteps] FP64,
+ * accumulated in FP64 on the device (Section 3.1 absorbing boundary; Eq. 1's mu_a term):
+ *   N_t       photon energy in the box after the step, N = sum_v h^3 n_v / c0 sum_d w I
+ *             (radiance I carries energy density I / c per unit solid angle, c = c0 / n);
+ *   escaped   energy leaving through the faces in the step, sum of w (Omega . n_out) I h^2 dt
+ *             over face voxels and outgoing directions;
+ *   absorbed  energy absorbed in the step, h^3 dt sum_v mu_a sum_d w I (rate mu_a c times N);
+ *   residual  the photon balance after the step: (energy before step 0) + (energy injected
+ *             by the source so far) - (escaped and absorbed so far) - N_t.  It measures the
+ *             discrete scheme's departure from photon conservation, not rounding: zero
+ *             (to FP32 rounding of the fields) once the light has left a box without
+ *             absorption; while a short pulse is in flight it oscillates, since N counts
+ *             ray samples and a sample sees the pulse once per retarded delay.
+ * Any pointer may be NULL. */
+int trinity_read_energy(trinity_ctx* ctx, double* N_t, double* escaped, double* absorbed, double* residual,
+                        size_t nsteps);
 
 /* Per-step iteration statistics of the last ``nsteps`` steps: max and mean per voxel. */
 int trinity_read_iterations(trinity_ctx* ctx, int* iters_max, double* iters_mean, size_t nsteps);
@@ -200,8 +219,12 @@ int trinity_read_iterations(trinity_ctx* ctx, int* iters_max, double* iters_mean
  * idle work.  Zero in the other modes (they do not count it). */
 int trinity_read_executed_iterations(trinity_ctx* ctx, double* executed_mean, size_t nsteps);
 
-/* Copy a field (TRINITY_FIELD_I or _S) at time level (steps_done - 1 - back),
- * 0 <= back <= 4, into ``out`` ([N_a][nz*ny*nx] float32, ``bytes`` = its size). */
+/* Copy a field at time level (steps_done - 1 - back), 0 <= back <= 4, into ``out``
+ * (``bytes`` = its size): TRINITY_FIELD_I or _S, [N_a][nz*ny*nx] float32 (S on the
+ * source function's directions); or TRINITY_FIELD_U, the photon energy density per voxel
+ * u = (n / c0) sum_d w I (the quantity whose maps Section 3.1 shows), [nz*ny*nx] float32,
+ * summed in FP64 on the device.  Reading U uses the context's scratch for Q: call it
+ * between steps, not while steps are queued on another thread. */
 int trinity_read_field(trinity_ctx* ctx, int what, int back, void* out, size_t bytes, int ptr_kind);
 
 /* Steps completed so far. */

@@ -13,9 +13,9 @@ from . import _lib
 from ._lib import GridDesc, TrinityError, OK, W_NOT_CONVERGED
 
 FP32, BF16 = 0, 1
-FIELD_I, FIELD_S = 0, 1
+FIELD_I, FIELD_S, FIELD_U = 0, 1, 2
 _PREC = {"fp32": FP32, "bf16": BF16}
-_BOUND = {"vacuum": 0, "periodic": 1}
+_BOUND = {"vacuum": 0, "periodic": 1, "mirror": 2}
 
 __all__ = ["Forward", "Server", "TrinityError", "grid_desc", "footprint_bytes",
            "adjoint_footprint_bytes", "healpix_dirs",
@@ -231,12 +231,19 @@ class Forward:
         return out
 
     def energy(self, nsteps=None):
+        """(N(t), escaped) per step of the last ``nsteps`` steps."""
+        b = self.balance(nsteps)
+        return b["energy"], b["escaped"]
+
+    def balance(self, nsteps=None):
+        """Photon accounting per step (FP64, from the device): energy in the box, escaped,
+        absorbed, and the balance residual (see trinity_read_energy)."""
         nsteps = self.steps_done() if nsteps is None else nsteps
-        N = np.zeros(nsteps)
-        E = np.zeros(nsteps)
-        self._check(self.L.trinity_read_energy(self.h, N.ctypes.data_as(_lib.P_double),
-                                               E.ctypes.data_as(_lib.P_double), nsteps))
-        return N, E
+        out = {k: np.zeros(nsteps) for k in ("energy", "escaped", "absorbed", "residual")}
+        self._check(self.L.trinity_read_energy(self.h, *(out[k].ctypes.data_as(_lib.P_double)
+                                                         for k in ("energy", "escaped", "absorbed",
+                                                                   "residual")), nsteps))
+        return out
 
     def iterations(self, nsteps=None):
         nsteps = self.steps_done() if nsteps is None else nsteps
@@ -256,12 +263,16 @@ class Forward:
 
     def field(self, what=FIELD_I, back=0, out=None):
         """Field at level steps_done-1-back as a host array [N_a, N_v] (or into a CUDA tensor);
-        S has the source function's N_a (coarser on a two-level angular grid)."""
+        S has the source function's N_a (coarser on a two-level angular grid); FIELD_U is the
+        energy density per voxel, [N_v]."""
         if out is not None and getattr(out, "is_cuda", False):
             self._check(self.L.trinity_read_field(self.h, what, back, ctypes.c_void_p(out.data_ptr()),
                                                   out.numel() * 4, 1))
             return out
-        arr = np.empty((self.na_s if what == FIELD_S else self.na, self.nv), dtype=np.float32)
+        if what == FIELD_U:
+            arr = np.empty(self.nv, dtype=np.float32)
+        else:
+            arr = np.empty((self.na_s if what == FIELD_S else self.na, self.nv), dtype=np.float32)
         self._check(self.L.trinity_read_field(self.h, what, back, arr.ctypes.data_as(ctypes.c_void_p),
                                               arr.nbytes, 0))
         return arr

@@ -115,8 +115,9 @@ __global__ void adj_inject_kernel(const int* __restrict__ det_vox, const int* __
 // Transposed scattering solve, FP32 on CUDA cores.  Same tiling and iteration as the
 // forward FP32 kernel (a CTA owns 16 voxels, thread i owns direction i, blocked sums of
 // P X with the diagonal row-sum correction r_i, y = (1 - eps) (P X + r X), the same stop
-// rule with a stall exit) with q = Sbar_n + b1 Ibar_n and a warm start from the previous
-// reverse step's y.  The epilogue writes Qbar = Ibar_n + y, clears the consumed adjoint
+// rule with a stall exit, the same isotropic rebalance after each plain update) with
+// q = Sbar_n + b1 Ibar_n and a warm start from the previous reverse step's y.  The
+// epilogue writes Qbar = Ibar_n + y, clears the consumed adjoint
 // level, and adds the voxel's dL/da and the b1 part of dL/dmu_t to the FP64 sums.
 // ----------------------------------------------------------------------------------------
 constexpr int kTile = 16;  // voxels per CTA: small enough for two CTAs per SM
@@ -143,7 +144,8 @@ __global__ void __launch_bounds__(AdjCfg<NA>::kThreads, 2)
   __shared__ __align__(16) float Xs[2][NA][kXStride];
   __shared__ float red_d[W][32];  // per warp, lane v < kTile holds voxel v's reduction
   __shared__ float red_s[W][32];
-  __shared__ float e_s[kTile], rho_s[kTile], best_s[kTile];
+  __shared__ float red_c[W][32];
+  __shared__ float e_s[kTile], rho_s[kTile], best_s[kTile], den_s[kTile], c_s[kTile];
   __shared__ int stall_s[kTile], iters_s[kTile];
   __shared__ unsigned act_s;
 
@@ -194,6 +196,21 @@ __global__ void __launch_bounds__(AdjCfg<NA>::kThreads, 2)
       *reinterpret_cast<float4*>(&Xs[0][i][v]) = x4;
     }
   }
+  {
+    // rebalance denominators sum_j (1 - a b1_j) per voxel
+    float bsum[kTile];
+#pragma unroll
+    for (int v = 0; v < kTile; ++v) bsum[v] = b1[v];
+    red_c[warp][lane] = warp_transpose<false>(bsum, lane);
+  }
+  __syncthreads();
+  if (tid < kTile) {
+    float sb = 0.0f;
+#pragma unroll
+    for (int w = 0; w < W; ++w) sb += red_c[w][tid];
+    den_s[tid] = static_cast<float>(NA) - (1.0f - e_s[tid]) * sb;
+    c_s[tid] = 0.0f;
+  }
   unsigned act = act_s;
   int cur = 0;
   int k = 0;
@@ -230,27 +247,21 @@ __global__ void __launch_bounds__(AdjCfg<NA>::kThreads, 2)
         for (int v = 0; v < kTile; ++v) acc[v] += t[v];
       }
     }
-    float dsv[kTile], smv[kTile];
+    float dsv[kTile], smv[kTile], cvv[kTile];
 #pragma unroll
     for (int v = 0; v < kTile; ++v) {
       const bool on = live && ((act >> v) & 1u);
       acc[v] = fmaf(ri, fmaf(b1[v], so[v], q[v]), acc[v]);  // (P + diag r) X
       const float yn = fmaf(-e_s[v], acc[v], acc[v]);
-      dsv[v] = on ? fabsf(yn - so[v]) : 0.0f;
+      const float dl = yn - so[v];
+      dsv[v] = on ? fabsf(dl) : 0.0f;
       smv[v] = on ? fabsf(yn) : 0.0f;
+      cvv[v] = on ? b1[v] * dl : 0.0f;
       so[v] = on ? yn : so[v];
-    }
-    const int nxt = cur ^ 1;
-    if (live) {
-#pragma unroll
-      for (int v = 0; v < kTile; v += 4) {
-        float4 x4 = make_float4(q[v] + b1[v] * so[v], q[v + 1] + b1[v + 1] * so[v + 1],
-                                q[v + 2] + b1[v + 2] * so[v + 2], q[v + 3] + b1[v + 3] * so[v + 3]);
-        *reinterpret_cast<float4*>(&Xs[nxt][i][v]) = x4;
-      }
     }
     red_d[warp][lane] = warp_transpose<true>(dsv, lane);
     red_s[warp][lane] = warp_transpose<true>(smv, lane);
+    red_c[warp][lane] = warp_transpose<false>(cvv, lane);
     __syncthreads();
     if (tid < 32) {  // one full warp: the ballot below is warp-collective
       const int v = tid;
@@ -270,16 +281,34 @@ __global__ void __launch_bounds__(AdjCfg<NA>::kThreads, 2)
         } else {
           stall_s[v] += 1;
         }
-        if ((r / (1.0f - r)) * D <= tol * scale || stall_s[v] >= 3) {
+        const bool stop = (r / (1.0f - r)) * D <= tol * scale || stall_s[v] >= 3;
+        if (stop) {
           done = 1u;
           iters_s[v] = k;
         }
+        float cs = 0.0f;
+#pragma unroll
+        for (int w = 0; w < W; ++w) cs += red_c[w][v];
+        c_s[v] = stop ? 0.0f : (1.0f - e_s[v]) * cs / den_s[v];
       }
       const unsigned mask = __ballot_sync(0xffffffffu, done);
       if (tid == 0) act_s = act & ~mask;
     }
     __syncthreads();
+    const unsigned was = act;
     act = act_s;
+    const int nxt = cur ^ 1;
+    if (live) {
+#pragma unroll
+      for (int v = 0; v < kTile; ++v)
+        if ((was >> v) & 1u) so[v] += c_s[v];
+#pragma unroll
+      for (int v = 0; v < kTile; v += 4) {
+        float4 x4 = make_float4(q[v] + b1[v] * so[v], q[v + 1] + b1[v + 1] * so[v + 1],
+                                q[v + 2] + b1[v + 2] * so[v + 2], q[v + 3] + b1[v + 3] * so[v + 3]);
+        *reinterpret_cast<float4*>(&Xs[nxt][i][v]) = x4;
+      }
+    }
     cur = nxt;
   }
   if (tid < kTile && ((act >> tid) & 1u)) iters_s[tid] = k;

@@ -69,6 +69,11 @@ struct trinity_ctx {
   unsigned long long* d_tile_iters = nullptr;
   double* d_energy = nullptr;
   double* d_escaped = nullptr;
+  double* d_absorbed = nullptr;
+  double* d_residual = nullptr;
+  double* d_balance = nullptr;   // [1] running photon balance (see advance_kernel)
+  double energy_init = 0.0;      // energy of the state before step 0
+  int* d_refl = nullptr;         // [na][8] reflected directions (mirror faces)
   int* d_bins = nullptr;
   int capacity = 0;
   int steps_done = 0;  // steps queued so far
@@ -76,6 +81,7 @@ struct trinity_ctx {
 
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
+  GridParams graph_g{}, graph_gs{};  // the parameters the captured kernels were given
 
   // two-level angular grid: S on na_s coarse directions, each the mean of nch children
   int na_s = 0;              // directions of S (= g.na on one grid)
@@ -92,6 +98,7 @@ struct trinity_ctx {
   int n_xcls = 0;
   float* d_Mt = nullptr;       // [classes][na][na] operators M = (I - a P B1)^-1 a P, transposed
   float* d_b1tab = nullptr;    // [classes][na] b1 of each class and direction
+  float* d_xmua = nullptr;     // [classes] mu_a of each class (absorbed-energy tally)
   uint8_t* d_xcls = nullptr;   // [nv] optics class of each voxel
   std::vector<float> h_P32, h_rc32, h_mut, h_eps;  // host copies the operators are built from
 
@@ -122,6 +129,7 @@ struct trinity_ctx {
   int* d_re_iters_max = nullptr;
   unsigned long long* d_re_iters_sum = nullptr;
   double *d_re_energy = nullptr, *d_re_escaped = nullptr, *d_re_det = nullptr;
+  double *d_re_absorbed = nullptr, *d_re_residual = nullptr, *d_re_balance = nullptr;
   int* d_re_nonconv = nullptr;
   int re_capacity = 0;
 };
@@ -174,7 +182,8 @@ bool desc_valid(const trinity_grid_desc* d, std::string* why) {
     *why = "two-level grid: nside_scatter 1, 2 or 4 and nside 2..16 a multiple of it";
     return false;
   }
-  if (d->boundary != TRINITY_BOUNDARY_VACUUM && d->boundary != TRINITY_BOUNDARY_PERIODIC) {
+  if (d->boundary != TRINITY_BOUNDARY_VACUUM && d->boundary != TRINITY_BOUNDARY_PERIODIC &&
+      d->boundary != TRINITY_BOUNDARY_MIRROR) {
     *why = "unknown boundary";
     return false;
   }
@@ -218,6 +227,9 @@ RunState run_state(trinity_ctx* c) {
   rs.tile_iters = c->d_tile_iters;
   rs.energy = c->d_energy;
   rs.escaped = c->d_escaped;
+  rs.absorbed = c->d_absorbed;
+  rs.residual = c->d_residual;
+  rs.balance = c->d_balance;
   rs.nonconv = c->d_nonconv;
   rs.bins = c->d_bins;
   rs.error = c->d_error;
@@ -232,33 +244,43 @@ int ensure_capacity(trinity_ctx* ctx, int need) {
   while (cap < need) cap *= 2;
   int* im = nullptr;
   unsigned long long *is = nullptr, *ti = nullptr;
-  double *en = nullptr, *es = nullptr;
+  double *en = nullptr, *es = nullptr, *ab = nullptr, *re = nullptr;
   int* bins = nullptr;
   CK(cudaStreamSynchronize(ctx->stream));
   CK(dalloc(&im, cap));
   CK(dalloc(&is, cap));
   CK(dalloc(&ti, cap));
-  CK(cudaMemset(ti, 0, cap * sizeof(unsigned long long)));
   CK(dalloc(&en, cap));
   CK(dalloc(&es, cap));
+  CK(dalloc(&ab, cap));
+  CK(dalloc(&re, cap));
   CK(dalloc(&bins, cap));
-  CK(cudaMemset(im, 0, cap * sizeof(int)));
-  CK(cudaMemset(is, 0, cap * sizeof(unsigned long long)));
-  CK(cudaMemset(en, 0, cap * sizeof(double)));
-  CK(cudaMemset(es, 0, cap * sizeof(double)));
+  // clears and copies on the context's stream: ordered with the kernels that follow
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemsetAsync(ti, 0, cap * sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(im, 0, cap * sizeof(int), st));
+  CK(cudaMemsetAsync(is, 0, cap * sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(en, 0, cap * sizeof(double), st));
+  CK(cudaMemsetAsync(es, 0, cap * sizeof(double), st));
+  CK(cudaMemsetAsync(ab, 0, cap * sizeof(double), st));
+  CK(cudaMemsetAsync(re, 0, cap * sizeof(double), st));
   if (ctx->capacity > 0) {
-    CK(cudaMemcpy(im, ctx->d_iters_max, ctx->capacity * sizeof(int), cudaMemcpyDeviceToDevice));
-    CK(cudaMemcpy(is, ctx->d_iters_sum, ctx->capacity * sizeof(unsigned long long),
-                  cudaMemcpyDeviceToDevice));
-    CK(cudaMemcpy(ti, ctx->d_tile_iters, ctx->capacity * sizeof(unsigned long long),
-                  cudaMemcpyDeviceToDevice));
-    CK(cudaMemcpy(en, ctx->d_energy, ctx->capacity * sizeof(double), cudaMemcpyDeviceToDevice));
-    CK(cudaMemcpy(es, ctx->d_escaped, ctx->capacity * sizeof(double), cudaMemcpyDeviceToDevice));
+    const size_t c0 = static_cast<size_t>(ctx->capacity);
+    CK(cudaMemcpyAsync(im, ctx->d_iters_max, c0 * sizeof(int), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(is, ctx->d_iters_sum, c0 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ti, ctx->d_tile_iters, c0 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(en, ctx->d_energy, c0 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(es, ctx->d_escaped, c0 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ab, ctx->d_absorbed, c0 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(re, ctx->d_residual, c0 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaStreamSynchronize(st));
     cudaFree(ctx->d_iters_max);
     cudaFree(ctx->d_iters_sum);
     cudaFree(ctx->d_tile_iters);
     cudaFree(ctx->d_energy);
     cudaFree(ctx->d_escaped);
+    cudaFree(ctx->d_absorbed);
+    cudaFree(ctx->d_residual);
     cudaFree(ctx->d_bins);
   }
   // detector bin of every step: floor((n + 1/2) dt / bin), integers snapped (FP64)
@@ -268,12 +290,15 @@ int ensure_capacity(trinity_ctx* ctx, int need) {
     const long b = floor_snap((n + 0.5) * ctx->dt / bw);
     hb[n] = (b >= 0 && b < ctx->nbins) ? static_cast<int>(b) : -1;
   }
-  CK(cudaMemcpy(bins, hb.data(), cap * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpyAsync(bins, hb.data(), cap * sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
   ctx->d_iters_max = im;
   ctx->d_iters_sum = is;
   ctx->d_tile_iters = ti;
   ctx->d_energy = en;
   ctx->d_escaped = es;
+  ctx->d_absorbed = ab;
+  ctx->d_residual = re;
   ctx->d_bins = bins;
   ctx->capacity = cap;
   if (ctx->graph) {
@@ -315,6 +340,22 @@ int lock_inputs(trinity_ctx* ctx) {
   CK(cudaMemset(ctx->d_det, 0, ndet * sizeof(double)));
   CK(cudaMemcpy(ctx->d_dirs, ctx->hdirs.data(), ctx->hdirs.size() * sizeof(DirInfo),
                 cudaMemcpyHostToDevice));
+  // the photon balance starts from the energy of the state held before step 0
+  ctx->energy_init = 0.0;
+  if (ctx->has_init) {
+    const size_t nv = ctx->g.nv, na = ctx->g.na;
+    std::vector<float> I0(na * nv);
+    CK(cudaMemcpy(I0.data(), ctx->I + static_cast<size_t>(ring_slot(-1)) * na * nv, na * nv * 4,
+                  cudaMemcpyDeviceToHost));
+    double e = 0.0;
+    for (size_t v = 0; v < nv; ++v) {
+      double sv = 0.0;
+      for (size_t d = 0; d < na; ++d) sv += I0[d * nv + v];
+      e += sv * ctx->nmap[v];
+    }
+    ctx->energy_init = e * static_cast<double>(ctx->g.e_scale);  // the factor the kernels use
+  }
+  CK(cudaMemcpy(ctx->d_balance, &ctx->energy_init, sizeof(double), cudaMemcpyHostToDevice));
   ctx->locked = true;
   return TRINITY_OK;
 }
@@ -406,13 +447,15 @@ void free_adjoint(trinity_ctx* c) {
                   c->d_gA,        c->d_gmut,        c->d_gmua,        c->d_gmus,
                   c->d_G,         c->d_ymax,        c->d_adj_nonconv, c->d_re_iters_max,
                   c->d_re_iters_sum, c->d_re_energy, c->d_re_escaped, c->d_re_det,
-                  c->d_re_nonconv, c->d_adj_iters};
+                  c->d_re_nonconv, c->d_adj_iters, c->d_re_absorbed, c->d_re_residual,
+                  c->d_re_balance};
   for (void* p : bufs)
     if (p) cudaFree(p);
   c->d_ckpt = c->d_stI = c->d_stS = c->d_aI = c->d_aS = c->d_Qb = c->d_Y = nullptr;
   c->d_ckpt_smax = c->d_ymax = nullptr;
   c->d_gA = c->d_gmut = c->d_gmua = c->d_gmus = c->d_G = nullptr;
   c->d_re_energy = c->d_re_escaped = c->d_re_det = nullptr;
+  c->d_re_absorbed = c->d_re_residual = c->d_re_balance = nullptr;
   c->d_adj_nonconv = c->d_re_iters_max = c->d_re_nonconv = nullptr;
   c->d_re_iters_sum = c->d_adj_iters = nullptr;
   c->re_capacity = 0;
@@ -476,7 +519,7 @@ int enqueue_transport(trinity_ctx* ctx, const RunState& rs) {
     CK(launch_sweep2(g, ctx->d_dirs, ctx->d_offs, ctx->d_children, ctx->nch, ctx->na_s, ctx->I, ctx->S,
                      ctx->mut, ctx->nidx, ctx->Q, ctx->Qc, rs, ctx->stream));
   } else {
-    CK(launch_sweep(g, ctx->d_dirs, ctx->d_offs, ctx->I, ctx->S, ctx->mut, ctx->nidx, ctx->Q, rs,
+    CK(launch_sweep(g, ctx->d_dirs, ctx->d_offs, ctx->I, ctx->S, ctx->mut, ctx->nidx, ctx->d_refl, ctx->Q, rs,
                     ctx->stream));
   }
   CK(launch_interface(ctx->n_iface, g.na, ctx->d_if_vox, ctx->d_if_rowptr, ctx->d_if_src, ctx->d_if_w,
@@ -491,8 +534,8 @@ int enqueue_transport(trinity_ctx* ctx, const RunState& rs) {
 int enqueue_scatter(trinity_ctx* ctx, const RunState& rs) {
   const GridParams& gs = ctx->g_s;
   if (ctx->exact) {
-    CK(launch_exact_fp32(gs, ctx->d_b1ds, ctx->nch, ctx->d_Mt, ctx->d_b1tab, ctx->d_xcls, ctx->Qc, ctx->mut,
-                         ctx->nidx, ctx->Ic, ctx->S, rs, ctx->stream));
+    CK(launch_exact_fp32(gs, ctx->d_b1ds, ctx->nch, ctx->d_Mt, ctx->d_b1tab, ctx->d_xcls, ctx->d_xmua, ctx->Qc,
+                         ctx->mut, ctx->nidx, ctx->Ic, ctx->S, rs, ctx->stream));
   } else if (ctx->desc.precision == TRINITY_BF16) {
     CK(launch_scatter_bf16(gs, bf_tables(ctx), ctx->Pbf, ctx->Qc, ctx->mut, ctx->eps, ctx->nidx, ctx->Ic,
                            ctx->S, static_cast<float>(ctx->desc.tol), ctx->desc.max_iters, rs,
@@ -513,7 +556,7 @@ int enqueue_finish(trinity_ctx* ctx, const RunState& rs, double* det) {
                      rs, ctx->stream));
   CK(launch_tally(g, ctx->d_dirs, ctx->I, ctx->d_det_vox, ctx->d_det_dir, ctx->d_det_w,
                   ctx->d_det_id, ctx->n_det_entries, det, ctx->nbins, rs, ctx->stream));
-  CK(launch_advance(rs, ctx->stream));
+  CK(launch_advance(ctx->g, rs, ctx->stream));
   return TRINITY_OK;
 }
 
@@ -603,16 +646,22 @@ int build_exact(trinity_ctx* ctx) {
       for (int j = 0; j < na; ++j)
         Mt[(c * na + j) * static_cast<size_t>(na) + i] = static_cast<float>(M[static_cast<size_t>(i) * na + j]);
   }
+  // mu_a of each class, formed as the iteration kernels form it (eps * mu_t in FP32)
+  std::vector<float> xmua(pairs.size());
+  for (size_t c = 0; c < pairs.size(); ++c) xmua[c] = pairs[c].second * pairs[c].first;
   cudaFree(ctx->d_Mt);
   cudaFree(ctx->d_xcls);
   cudaFree(ctx->d_b1tab);
-  cudaFree(ctx->d_b1tab);
+  cudaFree(ctx->d_xmua);
   ctx->d_Mt = nullptr;
   ctx->d_xcls = nullptr;
   ctx->d_b1tab = nullptr;
+  ctx->d_xmua = nullptr;
   CK(dalloc(&ctx->d_Mt, Mt.size()));
   CK(dalloc(&ctx->d_xcls, nv));
   CK(dalloc(&ctx->d_b1tab, b1tab.size()));
+  CK(dalloc(&ctx->d_xmua, xmua.size()));
+  CK(cudaMemcpy(ctx->d_xmua, xmua.data(), xmua.size() * 4, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_Mt, Mt.data(), Mt.size() * 4, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_b1tab, b1tab.data(), b1tab.size() * 4, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_xcls, cls.data(), nv, cudaMemcpyHostToDevice));
@@ -662,6 +711,7 @@ int trinity_create_grid(const trinity_grid_desc* desc, void* cuda_stream, trinit
   g.nv = desc->nx * desc->ny * desc->nz;
   g.na = 12 * desc->nside * desc->nside;
   g.periodic = desc->boundary == TRINITY_BOUNDARY_PERIODIC;
+  g.mirror = desc->boundary == TRINITY_BOUNDARY_MIRROR;
   g.hist_from = 0;
   g.src_voxel = -1;
   g.pulse_steps = 0;
@@ -669,6 +719,8 @@ int trinity_create_grid(const trinity_grid_desc* desc, void* cuda_stream, trinit
   ctx->dt = desc->courant * desc->h_mm * desc->n_ref / kC0;
   ctx->w = 4.0 * 3.14159265358979323846 / g.na;
   g.e_scale = static_cast<float>(desc->h_mm * desc->h_mm * desc->h_mm / kC0 * ctx->w);
+  g.a_scale = desc->h_mm * desc->h_mm * desc->h_mm * ctx->dt * ctx->w;
+  g.inj_step = 0.0;
   g.mut_u = -1.0f;
   g.n_u = 0.0f;
   try {
@@ -735,6 +787,8 @@ int trinity_create_grid(const trinity_grid_desc* desc, void* cuda_stream, trinit
   ctx->g_s.na = ctx->na_s;
   ctx->g_s.e_scale = static_cast<float>(desc->h_mm * desc->h_mm * desc->h_mm / kC0 *
                                         (4.0 * 3.14159265358979323846 / ctx->na_s));
+  ctx->g_s.a_scale = desc->h_mm * desc->h_mm * desc->h_mm * ctx->dt * (4.0 * 3.14159265358979323846 / ctx->na_s);
+  if (g.mirror && ctx->two_level) return bail(TRINITY_E_UNSUPPORTED);  // the two-level sweep has no images
 
   const size_t nv = g.nv, na = g.na, na_s = ctx->na_s;
   if (dalloc(&ctx->I, kRing * na * nv) != cudaSuccess || dalloc(&ctx->S, kRing * na_s * nv) != cudaSuccess ||
@@ -745,6 +799,7 @@ int trinity_create_grid(const trinity_grid_desc* desc, void* cuda_stream, trinit
       dalloc(&ctx->d_offs, ctx->lat.off.size()) != cudaSuccess || dalloc(&ctx->d_step, 1) != cudaSuccess ||
       dalloc(&ctx->d_smax, 2) != cudaSuccess || dalloc(&ctx->d_nonconv, 1) != cudaSuccess ||
       dalloc(&ctx->d_error, 1) != cudaSuccess || dalloc(&ctx->d_tile_ctr, 2) != cudaSuccess ||
+      dalloc(&ctx->d_balance, 1) != cudaSuccess || (g.mirror && dalloc(&ctx->d_refl, 8 * na) != cudaSuccess) ||
       dalloc(&ctx->d_rcorr, na_s) != cudaSuccess || dalloc(&ctx->d_rcorr32, na_s) != cudaSuccess ||
       dalloc(&ctx->d_cls, na_s) != cudaSuccess || dalloc(&ctx->d_cls_ds, 16 * ctx->nch) != cudaSuccess ||
       dalloc(&ctx->d_children, children.size()) != cudaSuccess ||
@@ -757,6 +812,29 @@ int trinity_create_grid(const trinity_grid_desc* desc, void* cuda_stream, trinit
   if (!ctx->two_level) {
     ctx->Qc = ctx->Q;  // one grid: the scatter reads Q and writes I directly
     ctx->Ic = ctx->I;
+  }
+  if (g.mirror) {
+    // refl[d][mask]: the direction of Omega_d with the components of the axes in mask
+    // negated (the HEALPix pixel set is symmetric under every face reflection)
+    std::vector<int> refl(8 * na);
+    for (size_t d = 0; d < na; ++d)
+      for (int mask = 0; mask < 8; ++mask) {
+        double t[3];
+        for (int a = 0; a < 3; ++a) t[a] = ctx->dirs[3 * d + a] * (((mask >> a) & 1) ? -1.0 : 1.0);
+        int best = -1;
+        double bd = -2.0;
+        for (size_t e = 0; e < na; ++e) {
+          const double dot = t[0] * ctx->dirs[3 * e] + t[1] * ctx->dirs[3 * e + 1] + t[2] * ctx->dirs[3 * e + 2];
+          if (dot > bd) {
+            bd = dot;
+            best = static_cast<int>(e);
+          }
+        }
+        if (bd < 1.0 - 1e-12) return bail(TRINITY_E_INVALID);
+        refl[d * 8 + mask] = best;
+      }
+    if (cudaMemcpy(ctx->d_refl, refl.data(), refl.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(TRINITY_E_CUDA);
   }
   if (cudaMemcpy(ctx->d_offs, ctx->lat.off.data(), ctx->lat.off.size(), cudaMemcpyHostToDevice) !=
           cudaSuccess ||
@@ -935,7 +1013,7 @@ int trinity_set_source(trinity_ctx* ctx, int face, double u_mm, double v_mm, dou
                        int pulse_steps, double energy) {
   if (!ctx) return TRINITY_E_INVALID;
   if (ctx->locked) return fail(ctx, TRINITY_E_STATE, "source must be set before the first step");
-  if (ctx->g.periodic) return fail(ctx, TRINITY_E_INVALID, "a source needs vacuum boundaries");
+  if (ctx->g.periodic || ctx->g.mirror) return fail(ctx, TRINITY_E_INVALID, "a source needs vacuum boundaries");
   if (face < 0 || face > 5 || pulse_steps < 1 || !(energy >= 0.0))
     return fail(ctx, TRINITY_E_INVALID, "bad face, pulse_steps or energy");
   const int nn[3] = {ctx->g.nx, ctx->g.ny, ctx->g.nz};
@@ -953,6 +1031,7 @@ int trinity_set_source(trinity_ctx* ctx, int face, double u_mm, double v_mm, dou
   }
   const double h = ctx->desc.h_mm;
   const int entry_sgn = (face % 2 == 0) ? 1 : -1;
+  double inj = 0.0;
   for (int d = 0; d < ctx->g.na; ++d) {
     ctx->hdirs[d].src_amp = 0.0f;
     if (alpha[d] == 0.0) continue;
@@ -961,7 +1040,10 @@ int trinity_set_source(trinity_ctx* ctx, int face, double u_mm, double v_mm, dou
       return fail(ctx, TRINITY_E_INVALID, "source cone reaches a direction that does not enter through the face");
     const double amp = energy * alpha[d] / (ctx->w * cos_in * h * h * pulse_steps * ctx->dt);
     ctx->hdirs[d].src_amp = static_cast<float>(amp);
+    // the energy the FP32 amplitude actually carries in per pulse step
+    inj += static_cast<double>(ctx->hdirs[d].src_amp) * ctx->w * cos_in * h * h * ctx->dt;
   }
+  ctx->g.inj_step = inj;
   int c[3];
   c[ax] = (face % 2) ? nn[ax] - 1 : 0;
   c[ua] = static_cast<int>(iu);
@@ -1028,12 +1110,16 @@ int trinity_set_bins(trinity_ctx* ctx, double bin_ps, int nbins) {
     cudaFree(ctx->d_tile_iters);
     cudaFree(ctx->d_energy);
     cudaFree(ctx->d_escaped);
+    cudaFree(ctx->d_absorbed);
+    cudaFree(ctx->d_residual);
     cudaFree(ctx->d_bins);
     ctx->d_iters_max = nullptr;
     ctx->d_iters_sum = nullptr;
     ctx->d_tile_iters = nullptr;
     ctx->d_energy = nullptr;
     ctx->d_escaped = nullptr;
+    ctx->d_absorbed = nullptr;
+    ctx->d_residual = nullptr;
     ctx->d_bins = nullptr;
     return ensure_capacity(ctx, cap);
   }
@@ -1099,6 +1185,13 @@ int trinity_run(trinity_ctx* ctx, int nsteps) {
   rc = ensure_capacity(ctx, ctx->steps_done + nsteps);
   if (rc != TRINITY_OK) return rc;
   constexpr int kGraphSteps = 8;
+  // kernels take the grid parameters by value: a change (e.g. an initial state after a
+  // reset) needs a new capture
+  if (ctx->graph && (std::memcmp(&ctx->graph_g, &ctx->g, sizeof(GridParams)) != 0 ||
+                     std::memcmp(&ctx->graph_gs, &ctx->g_s, sizeof(GridParams)) != 0)) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
   if (!ctx->graph) {
     cudaStream_t cap_stream;
     CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
@@ -1117,6 +1210,8 @@ int trinity_run(trinity_ctx* ctx, int nsteps) {
     cudaGraphDestroy(graph);
     CK(ce);
     ctx->graph_steps = kGraphSteps;
+    ctx->graph_g = ctx->g;
+    ctx->graph_gs = ctx->g_s;
   }
   int left = nsteps;
   while (left >= ctx->graph_steps) {
@@ -1182,6 +1277,7 @@ int trinity_run_checkpointed(trinity_ctx* ctx, int nsteps, int every) {
   if (nsteps < 1 || every < 1) return fail(ctx, TRINITY_E_INVALID, "nsteps and every must be >= 1");
   if (ctx->two_level)
     return fail(ctx, TRINITY_E_UNSUPPORTED, "the adjoint covers one angular grid (nside_scatter = nside)");
+  if (ctx->g.mirror) return fail(ctx, TRINITY_E_UNSUPPORTED, "the adjoint covers vacuum and periodic boundaries");
   if (ctx->steps_done != 0)
     return fail(ctx, TRINITY_E_STATE, "a checkpointed run starts at step 0 (call trinity_reset)");
   int rc = lock_inputs(ctx);
@@ -1250,7 +1346,9 @@ int adjoint_impl(trinity_ctx* ctx, const double* dL_dE, size_t n, double* grad_m
               dalloc(&ctx->d_re_iters_max, N) == cudaSuccess &&
               dalloc(&ctx->d_re_iters_sum, N) == cudaSuccess &&
               dalloc(&ctx->d_re_energy, N) == cudaSuccess && dalloc(&ctx->d_re_escaped, N) == cudaSuccess &&
-              dalloc(&ctx->d_re_det, ndb) == cudaSuccess && dalloc(&ctx->d_re_nonconv, 1) == cudaSuccess;
+              dalloc(&ctx->d_re_det, ndb) == cudaSuccess && dalloc(&ctx->d_re_nonconv, 1) == cudaSuccess &&
+              dalloc(&ctx->d_re_absorbed, N) == cudaSuccess && dalloc(&ctx->d_re_residual, N) == cudaSuccess &&
+              dalloc(&ctx->d_re_balance, 1) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
       return fail(ctx, TRINITY_E_OOM, "no device memory for the adjoint buffers");
@@ -1273,12 +1371,18 @@ int adjoint_impl(trinity_ctx* ctx, const double* dL_dE, size_t n, double* grad_m
   CK(cudaMemsetAsync(ctx->d_re_iters_sum, 0, N * sizeof(unsigned long long), ctx->stream));
   CK(cudaMemsetAsync(ctx->d_re_energy, 0, N * sizeof(double), ctx->stream));
   CK(cudaMemsetAsync(ctx->d_re_escaped, 0, N * sizeof(double), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_re_absorbed, 0, N * sizeof(double), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_re_residual, 0, N * sizeof(double), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_re_balance, 0, sizeof(double), ctx->stream));
   RunState rs = run_state(ctx);  // recomputed steps: same step counter, smax and bins
   rs.iters_max = ctx->d_re_iters_max;
   rs.iters_sum = ctx->d_re_iters_sum;
   rs.tile_iters = nullptr;
   rs.energy = ctx->d_re_energy;
   rs.escaped = ctx->d_re_escaped;
+  rs.absorbed = ctx->d_re_absorbed;
+  rs.residual = ctx->d_re_residual;
+  rs.balance = ctx->d_re_balance;
   rs.nonconv = ctx->d_re_nonconv;
   const double bw = ctx->bin_ps * 1e-3;
   const float tol = static_cast<float>(ctx->desc.tol);
@@ -1426,14 +1530,18 @@ int trinity_read_detectors(trinity_ctx* ctx, double* out, size_t n) {
   return TRINITY_OK;
 }
 
-int trinity_read_energy(trinity_ctx* ctx, double* N_t, double* escaped, size_t nsteps) {
+int trinity_read_energy(trinity_ctx* ctx, double* N_t, double* escaped, double* absorbed, double* residual,
+                        size_t nsteps) {
   if (!ctx) return TRINITY_E_INVALID;
   if (nsteps > static_cast<size_t>(ctx->steps_done)) return fail(ctx, TRINITY_E_INVALID, "more steps than done");
   if (nsteps == 0) return TRINITY_OK;
   const size_t first = ctx->steps_done - nsteps;
   CK(cudaStreamSynchronize(ctx->stream));
-  if (N_t) CK(cudaMemcpy(N_t, ctx->d_energy + first, nsteps * sizeof(double), cudaMemcpyDeviceToHost));
-  if (escaped) CK(cudaMemcpy(escaped, ctx->d_escaped + first, nsteps * sizeof(double), cudaMemcpyDeviceToHost));
+  const size_t b = nsteps * sizeof(double);
+  if (N_t) CK(cudaMemcpy(N_t, ctx->d_energy + first, b, cudaMemcpyDeviceToHost));
+  if (escaped) CK(cudaMemcpy(escaped, ctx->d_escaped + first, b, cudaMemcpyDeviceToHost));
+  if (absorbed) CK(cudaMemcpy(absorbed, ctx->d_absorbed + first, b, cudaMemcpyDeviceToHost));
+  if (residual) CK(cudaMemcpy(residual, ctx->d_residual + first, b, cudaMemcpyDeviceToHost));
   return TRINITY_OK;
 }
 
@@ -1466,9 +1574,11 @@ int trinity_read_executed_iterations(trinity_ctx* ctx, double* executed_mean, si
 
 int trinity_read_field(trinity_ctx* ctx, int what, int back, void* out, size_t bytes, int ptr_kind) {
   if (!ctx) return TRINITY_E_INVALID;
-  const size_t cnt = static_cast<size_t>(what == TRINITY_FIELD_S ? ctx->na_s : ctx->g.na) * ctx->g.nv;
-  if ((what != TRINITY_FIELD_I && what != TRINITY_FIELD_S) || back < 0 || back > kRing - 1 ||
-      bytes != cnt * 4 || !out || (ptr_kind != 0 && ptr_kind != 1))
+  const size_t nv = ctx->g.nv;
+  const size_t cnt = what == TRINITY_FIELD_U ? nv
+                                             : static_cast<size_t>(what == TRINITY_FIELD_S ? ctx->na_s : ctx->g.na) * nv;
+  if ((what != TRINITY_FIELD_I && what != TRINITY_FIELD_S && what != TRINITY_FIELD_U) || back < 0 ||
+      back > kRing - 1 || bytes != cnt * 4 || !out || (ptr_kind != 0 && ptr_kind != 1))
     return fail(ctx, TRINITY_E_INVALID, "bad field request");
   const int lev = ctx->steps_done - 1 - back;
   CK(cudaStreamSynchronize(ctx->stream));
@@ -1478,6 +1588,15 @@ int trinity_read_field(trinity_ctx* ctx, int what, int back, void* out, size_t b
       CK(cudaMemset(out, 0, bytes));
     else
       std::memset(out, 0, bytes);
+    return TRINITY_OK;
+  }
+  if (what == TRINITY_FIELD_U) {
+    // energy density of level lev, formed in the context's Q buffer (free between steps)
+    const float* Ilev = ctx->I + static_cast<size_t>(ring_slot(lev)) * ctx->g.na * nv;
+    const float scale = static_cast<float>(ctx->w / kC0);
+    CK(launch_energy_density(ctx->g, Ilev, ctx->nidx, scale, ctx->Q, ctx->stream));
+    CK(cudaMemcpyAsync(out, ctx->Q, bytes, kind, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     return TRINITY_OK;
   }
   const float* base = (what == TRINITY_FIELD_I ? ctx->I : ctx->S) + static_cast<size_t>(ring_slot(lev)) * cnt;
@@ -1495,36 +1614,42 @@ int trinity_reset(trinity_ctx* ctx) {
   if (!ctx) return TRINITY_E_INVALID;
   const size_t cnt = static_cast<size_t>(ctx->g.na) * ctx->g.nv;
   const size_t cnt_s = static_cast<size_t>(ctx->na_s) * ctx->g.nv;
-  CK(cudaStreamSynchronize(ctx->stream));
-  CK(cudaMemset(ctx->I, 0, kRing * cnt * 4));
-  CK(cudaMemset(ctx->S, 0, kRing * cnt_s * 4));
-  CK(cudaMemset(ctx->Q, 0, cnt * 4));
+  // every clear runs on the context's stream, so work queued on it afterwards sees it
+  cudaStream_t st = ctx->stream;
+  CK(cudaStreamSynchronize(st));
+  CK(cudaMemsetAsync(ctx->I, 0, kRing * cnt * 4, st));
+  CK(cudaMemsetAsync(ctx->S, 0, kRing * cnt_s * 4, st));
+  CK(cudaMemsetAsync(ctx->Q, 0, cnt * 4, st));
   if (ctx->two_level) {
-    CK(cudaMemset(ctx->Ic, 0, kRing * cnt_s * 4));
-    CK(cudaMemset(ctx->Qc, 0, cnt_s * 4));
+    CK(cudaMemsetAsync(ctx->Ic, 0, kRing * cnt_s * 4, st));
+    CK(cudaMemsetAsync(ctx->Qc, 0, cnt_s * 4, st));
   }
-  CK(cudaMemset(ctx->d_step, 0, sizeof(int)));
-  CK(cudaMemset(ctx->d_smax, 0, 2 * sizeof(unsigned)));
-  CK(cudaMemset(ctx->d_nonconv, 0, sizeof(int)));
-  CK(cudaMemset(ctx->d_error, 0, sizeof(int)));
-  CK(cudaMemset(ctx->d_tile_ctr, 0, 2 * sizeof(int)));
+  CK(cudaMemsetAsync(ctx->d_step, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(ctx->d_smax, 0, 2 * sizeof(unsigned), st));
+  CK(cudaMemsetAsync(ctx->d_nonconv, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(ctx->d_error, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(ctx->d_tile_ctr, 0, 2 * sizeof(int), st));
+  CK(cudaMemsetAsync(ctx->d_balance, 0, sizeof(double), st));
   if (ctx->capacity > 0) {
-    CK(cudaMemset(ctx->d_iters_max, 0, ctx->capacity * sizeof(int)));
-    CK(cudaMemset(ctx->d_iters_sum, 0, ctx->capacity * sizeof(unsigned long long)));
-    CK(cudaMemset(ctx->d_tile_iters, 0, ctx->capacity * sizeof(unsigned long long)));
-    CK(cudaMemset(ctx->d_energy, 0, ctx->capacity * sizeof(double)));
-    CK(cudaMemset(ctx->d_escaped, 0, ctx->capacity * sizeof(double)));
+    const size_t c = static_cast<size_t>(ctx->capacity);
+    CK(cudaMemsetAsync(ctx->d_iters_max, 0, c * sizeof(int), st));
+    CK(cudaMemsetAsync(ctx->d_iters_sum, 0, c * sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(ctx->d_tile_iters, 0, c * sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(ctx->d_energy, 0, c * sizeof(double), st));
+    CK(cudaMemsetAsync(ctx->d_escaped, 0, c * sizeof(double), st));
+    CK(cudaMemsetAsync(ctx->d_absorbed, 0, c * sizeof(double), st));
+    CK(cudaMemsetAsync(ctx->d_residual, 0, c * sizeof(double), st));
   }
-  if (ctx->d_det) CK(cudaMemset(ctx->d_det, 0, ctx->dets.size() * std::max(ctx->nbins, 1) * sizeof(double)));
+  if (ctx->d_det)
+    CK(cudaMemsetAsync(ctx->d_det, 0, ctx->dets.size() * std::max(ctx->nbins, 1) * sizeof(double), st));
+  CK(cudaStreamSynchronize(st));
   ctx->g.hist_from = 0;
   ctx->has_init = false;
   ctx->steps_done = 0;
   ctx->nonconv_seen = 0;
   free_adjoint(ctx);
-  if (ctx->graph) {
-    cudaGraphExecDestroy(ctx->graph);
-    ctx->graph = nullptr;
-  }
+  // the captured graph stays valid: buffers are unchanged, and trinity_run recaptures if
+  // the grid parameters changed
   return TRINITY_OK;
 }
 
@@ -1545,6 +1670,8 @@ void trinity_destroy(trinity_ctx* ctx) {
   cudaFree(ctx->d_b1ds);
   cudaFree(ctx->d_Mt);
   cudaFree(ctx->d_xcls);
+  cudaFree(ctx->d_b1tab);
+  cudaFree(ctx->d_xmua);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   void* bufs[] = {ctx->I,         ctx->S,          ctx->Q,           ctx->mut,       ctx->eps,
                   ctx->nidx,      ctx->P32,        ctx->Pbf,         ctx->d_dirs,    ctx->d_offs,
@@ -1552,7 +1679,7 @@ void trinity_destroy(trinity_ctx* ctx) {
                   ctx->d_step,    ctx->d_smax,     ctx->d_nonconv,   ctx->d_error,   ctx->d_iters_max,
                   ctx->d_iters_sum, ctx->d_energy, ctx->d_escaped,   ctx->d_bins, ctx->d_tile_iters,
                   ctx->d_tile_ctr, ctx->d_rcorr,   ctx->d_cls,       ctx->d_cls_ds,
-                  ctx->d_rcorr32};
+                  ctx->d_rcorr32, ctx->d_absorbed, ctx->d_residual,  ctx->d_balance, ctx->d_refl};
   for (void* p : bufs)
     if (p) cudaFree(p);
   delete ctx;

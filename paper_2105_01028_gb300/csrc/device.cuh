@@ -24,6 +24,7 @@ struct GridParams {
   int na;           // directions
   int nmax;         // stride of the offset table
   int periodic;
+  int mirror;       // mirror faces: a ghost upwind sample reads its image (see sweep.cu)
   int hist_from;    // first valid time level: 0, or -4 with an initial state
   int src_voxel;    // flat voxel index of the source spot, -1 if none
   int pulse_steps;
@@ -32,6 +33,8 @@ struct GridParams {
   float e_scale;    // h^3 / c0 * w  (energy per unit I * n)
   float mut_u;      // mu_t of every voxel when the medium's mu_t is uniform, else -1
   float n_u;        // n of every voxel when the refractive index is uniform, else 0
+  double a_scale;   // h^3 dt w: absorbed energy per unit I * mu_a in one step
+  double inj_step;  // energy the source's inflow carries in during each pulse step
 };
 
 // Per-run device counters and tallies (pointers into context-owned buffers).
@@ -42,6 +45,9 @@ struct RunState {
   unsigned long long* iters_sum; // [capacity] per step (sum over voxels)
   double* energy;                // [capacity] photon energy in the box after the step
   double* escaped;               // [capacity] energy leaving through the faces in the step
+  double* absorbed;              // [capacity] energy absorbed (mu_a term of Eq. 1) in the step
+  double* residual;              // [capacity] photon balance residual after the step
+  double* balance;               // [1] energy before step 0 + injected - escaped - absorbed
   int* nonconv;                  // count of voxel-steps that hit max_iters
   int* bins;                     // [capacity] detector bin of each step (-1: none)
   int* error;                    // device error word (0 = ok)
@@ -124,7 +130,7 @@ __device__ __forceinline__ float ray_b1(float x, float T) {
 // Kernel launchers (defined in kernels.cu / scatter_tc.cu).
 cudaError_t launch_sweep(const GridParams& g, const DirInfo* dirs, const int8_t* offs,
                          const float* Iring, const float* Sring, const float* mut,
-                         const float* nidx, float* Q, RunState rs, cudaStream_t st);
+                         const float* nidx, const int* refl, float* Q, RunState rs, cudaStream_t st);
 cudaError_t launch_scatter_fp32(const GridParams& g, const float* b1ds, int nch, const float* P,
                                 const float* rcorr, const float* Q, const float* mut,
                                 const float* eps,
@@ -134,7 +140,9 @@ cudaError_t launch_tally(const GridParams& g, const DirInfo* dirs, const float* 
                          const int* det_vox, const int* det_dir, const float* det_w,
                          const int* det_id, int n_det_entries, double* det, int nbins,
                          RunState rs, cudaStream_t st);
-cudaError_t launch_advance(RunState rs, cudaStream_t st);
+cudaError_t launch_advance(const GridParams& g, RunState rs, cudaStream_t st);
+cudaError_t launch_energy_density(const GridParams& g, const float* I, const float* nidx, float scale, float* u,
+                                  cudaStream_t st);
 cudaError_t launch_interface(int nvox, int na, const int* vox, const int* rowptr, const int* src,
                              const float* w, const uint8_t* keep, float* Q, int nv, cudaStream_t st);
 bool scatter_bf16_supported(int na);
@@ -189,8 +197,10 @@ namespace trinity {
 // Exact per-voxel source function for piecewise-uniform optics (defined in exact.cu).
 // Mt: [classes][na][na] FP32, M transposed; cls: [nv] class of each voxel (< 32).
 // b1tab: [classes][na] b1 of each class and direction (the 192-direction GEMM form uses it).
+// mua_cls: [classes] mu_a of each class (absorbed-energy tally).
 cudaError_t launch_exact_fp32(const GridParams& g, const float* b1ds, int nch, const float* Mt,
-                              const float* b1tab, const uint8_t* cls, const float* Q, const float* mut,
-                              const float* nidx, float* Iring, float* Sring, RunState rs, cudaStream_t st);
+                              const float* b1tab, const uint8_t* cls, const float* mua_cls, const float* Q,
+                              const float* mut, const float* nidx, float* Iring, float* Sring, RunState rs,
+                              cudaStream_t st);
 
 }  // namespace trinity

@@ -30,14 +30,15 @@ struct ExCfg {
 template <int NA>
 __global__ void __launch_bounds__(ExCfg<NA>::kThreads)
     exact_fp32_kernel(GridParams g, const float* __restrict__ b1ds, int nch, const float* __restrict__ Mt,
-                      const uint8_t* __restrict__ cls, const float* __restrict__ Q,
+                      const uint8_t* __restrict__ cls, const float* __restrict__ mua_cls,
+                      const float* __restrict__ Q,
                       const float* __restrict__ mut, const float* __restrict__ nidx,
                       float* __restrict__ Iring, float* __restrict__ Sring, RunState rs) {
   constexpr int W = ExCfg<NA>::kWarps;
   __shared__ __align__(16) float Xs[NA][kXStride];
   __shared__ int cls_s[kTile];
   __shared__ unsigned present_s;
-  __shared__ double esum_s[W];
+  __shared__ double esum_s[W], asum_s[W];
   __shared__ float smax_s[W];
 
   const int n = *rs.step;
@@ -111,7 +112,7 @@ __global__ void __launch_bounds__(ExCfg<NA>::kThreads)
   const size_t cur_off = (static_cast<size_t>(ring_slot(n)) * g.na + (live ? i : 0)) * plane;
   const float* dsl = b1ds + static_cast<size_t>(live ? i : 0) * nch;
   const float inv_nch = 1.0f / static_cast<float>(nch);
-  float esum = 0.0f, smax = 0.0f;
+  float esum = 0.0f, asum = 0.0f, smax = 0.0f;
   if (live) {
 #pragma unroll
     for (int v = 0; v < kTile; ++v) {
@@ -127,6 +128,7 @@ __global__ void __launch_bounds__(ExCfg<NA>::kThreads)
         Iring[cur_off + vv] = Iv;
         Sring[cur_off + vv] = s[v];
         esum = fmaf(Iv, nidx[vv], esum);
+        asum = fmaf(Iv, mua_cls[cls_s[v]], asum);
         smax = fmaxf(smax, fabsf(s[v]));
       }
     }
@@ -134,22 +136,26 @@ __global__ void __launch_bounds__(ExCfg<NA>::kThreads)
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) {
     esum += __shfl_xor_sync(0xffffffffu, esum, o);
+    asum += __shfl_xor_sync(0xffffffffu, asum, o);
     smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, o));
   }
   if (lane == 0) {
     esum_s[warp] = esum;
+    asum_s[warp] = asum;
     smax_s[warp] = smax;
   }
   __syncthreads();
   if (tid == 0) {
-    double e = 0.0;
+    double e = 0.0, ab = 0.0;
     float sm = 0.0f;
     for (int w = 0; w < W; ++w) {
       e += esum_s[w];
+      ab += asum_s[w];
       sm = fmaxf(sm, smax_s[w]);
     }
     int cnt = g.nv - v0 < kTile ? g.nv - v0 : kTile;
     atomicAdd(rs.energy + n, e * static_cast<double>(g.e_scale));
+    atomicAdd(rs.absorbed + n, ab * g.a_scale);
     atomicMax(rs.smax + (n & 1), __float_as_uint(sm));
     atomicMax(rs.iters_max + n, 1);
     atomicAdd(rs.iters_sum + n, static_cast<unsigned long long>(cnt));
@@ -172,7 +178,8 @@ constexpr int kGRi = 24;    // directions per warp
 
 __global__ void __launch_bounds__(256, 2)
     exact_gemm192_kernel(GridParams g, const float* __restrict__ Mt, const float* __restrict__ b1tab,
-                         const uint8_t* __restrict__ cls, const float* __restrict__ Q,
+                         const uint8_t* __restrict__ cls, const float* __restrict__ mua_cls,
+                         const float* __restrict__ Q,
                          const float* __restrict__ nidx, float* __restrict__ Iring,
                          float* __restrict__ Sring, RunState rs) {
   extern __shared__ __align__(16) float gsm[];
@@ -180,7 +187,7 @@ __global__ void __launch_bounds__(256, 2)
   float* Ms = gsm + kGNa * kGV;       // [16][192]
   __shared__ int cls_s[kGV];
   __shared__ unsigned present_s;
-  __shared__ double esum_s[8];
+  __shared__ double esum_s[8], asum_s[8];
   __shared__ float smax_s[8];
 
   const int n = *rs.step;
@@ -203,7 +210,7 @@ __global__ void __launch_bounds__(256, 2)
 
   const int vl0 = lane * 2, i0 = warp * kGRi;
   const size_t slot = static_cast<size_t>(ring_slot(n)) * g.na;
-  float esum = 0.0f, smax = 0.0f;
+  float esum = 0.0f, asum = 0.0f, smax = 0.0f;
   unsigned present = present_s;
   while (present != 0u) {
     const int c = __ffs(present) - 1;
@@ -243,6 +250,7 @@ __global__ void __launch_bounds__(256, 2)
       const int vl = vl0 + a, v = vb + vl;
       if (v >= g.nv || cls_s[vl] != c) continue;
       const float nv_idx = nidx[v];
+      const float ma = mua_cls[c];
 #pragma unroll
       for (int b = 0; b < kGRi; ++b) {
         const int i = i0 + b;
@@ -252,6 +260,7 @@ __global__ void __launch_bounds__(256, 2)
         Iring[o] = Iv;
         Sring[o] = sv;
         esum = fmaf(Iv, nv_idx, esum);
+        asum = fmaf(Iv, ma, asum);
         smax = fmaxf(smax, fabsf(sv));
       }
     }
@@ -259,22 +268,26 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) {
     esum += __shfl_xor_sync(0xffffffffu, esum, o);
+    asum += __shfl_xor_sync(0xffffffffu, asum, o);
     smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, o));
   }
   if (lane == 0) {
     esum_s[warp] = esum;
+    asum_s[warp] = asum;
     smax_s[warp] = smax;
   }
   __syncthreads();
   if (tid == 0) {
-    double e = 0.0;
+    double e = 0.0, ab = 0.0;
     float sm = 0.0f;
     for (int w = 0; w < 8; ++w) {
       e += esum_s[w];
+      ab += asum_s[w];
       sm = fmaxf(sm, smax_s[w]);
     }
     const int cnt = g.nv - vb < kGV ? g.nv - vb : kGV;
     atomicAdd(rs.energy + n, e * static_cast<double>(g.e_scale));
+    atomicAdd(rs.absorbed + n, ab * g.a_scale);
     atomicMax(rs.smax + (n & 1), __float_as_uint(sm));
     atomicMax(rs.iters_max + n, 1);
     atomicAdd(rs.iters_sum + n, static_cast<unsigned long long>(cnt));
@@ -284,8 +297,9 @@ __global__ void __launch_bounds__(256, 2)
 }  // namespace
 
 cudaError_t launch_exact_fp32(const GridParams& g, const float* b1ds, int nch, const float* Mt,
-                              const float* b1tab, const uint8_t* cls, const float* Q, const float* mut,
-                              const float* nidx, float* Iring, float* Sring, RunState rs, cudaStream_t st) {
+                              const float* b1tab, const uint8_t* cls, const float* mua_cls, const float* Q,
+                              const float* mut, const float* nidx, float* Iring, float* Sring, RunState rs,
+                              cudaStream_t st) {
   if (g.na == kGNa && b1tab) {
     constexpr size_t kDyn = (static_cast<size_t>(kGNa) * kGV + static_cast<size_t>(kGKc) * kGNa) * sizeof(float);
     static cudaError_t attr = [] {
@@ -298,21 +312,21 @@ cudaError_t launch_exact_fp32(const GridParams& g, const float* b1ds, int nch, c
     }();
     if (attr != cudaSuccess) return attr;
     const int blocks = (g.nv + kGV - 1) / kGV;
-    exact_gemm192_kernel<<<blocks, 256, kDyn, st>>>(g, Mt, b1tab, cls, Q, nidx, Iring, Sring, rs);
+    exact_gemm192_kernel<<<blocks, 256, kDyn, st>>>(g, Mt, b1tab, cls, mua_cls, Q, nidx, Iring, Sring, rs);
     return cudaGetLastError();
   }
   const int tiles = (g.nv + kTile - 1) / kTile;
   switch (g.na) {
     case 12:
-      exact_fp32_kernel<12><<<tiles, ExCfg<12>::kThreads, 0, st>>>(g, b1ds, nch, Mt, cls, Q, mut, nidx,
+      exact_fp32_kernel<12><<<tiles, ExCfg<12>::kThreads, 0, st>>>(g, b1ds, nch, Mt, cls, mua_cls, Q, mut, nidx,
                                                                    Iring, Sring, rs);
       break;
     case 48:
-      exact_fp32_kernel<48><<<tiles, ExCfg<48>::kThreads, 0, st>>>(g, b1ds, nch, Mt, cls, Q, mut, nidx,
+      exact_fp32_kernel<48><<<tiles, ExCfg<48>::kThreads, 0, st>>>(g, b1ds, nch, Mt, cls, mua_cls, Q, mut, nidx,
                                                                    Iring, Sring, rs);
       break;
     case 192:
-      exact_fp32_kernel<192><<<tiles, ExCfg<192>::kThreads, 0, st>>>(g, b1ds, nch, Mt, cls, Q, mut, nidx,
+      exact_fp32_kernel<192><<<tiles, ExCfg<192>::kThreads, 0, st>>>(g, b1ds, nch, Mt, cls, mua_cls, Q, mut, nidx,
                                                                      Iring, Sring, rs);
       break;
     default:

@@ -17,6 +17,18 @@ __device__ __forceinline__ int pick(int axis, int x, int y, int z) {
 // ----------------------------------------------------------------------------------------
 // Source iteration on CUDA cores (plain FP32 mode).
 // A CTA owns a tile of kTile voxels; thread i < NA owns outgoing direction i of all of them.
+// Isotropic rebalance (angular two-grid correction): after each plain update S_half of
+// S_k, the voxel's isotropic error component is removed.  The error of S_half,
+// f = S* - S_half, solves (1 - a P B1) f = a P B1 Delta with Delta = S_half - S_k; its
+// projection on the constant vector (P has unit column sums) gives the scalar
+//   c = a sum_j b1_j Delta_j / sum_j (1 - a b1_j),
+// and S_{k+1} = S_half + c.  The isotropic mode is the slowest of the plain iteration
+// (contraction a b1 ~ 0.93 at the workloads' optics); without it the iterate reaches the
+// FP32 noise floor ~1/(1 - a b1) ~ 14 noise units short of the fixed point, always on the
+// same side, and that bias accumulates over the steps.  The correction vanishes at the
+// fixed point, so the fixed point is the plain iteration's.  The stop test is taken on
+// the plain update (|S_half - S_k| bounds the error of S_half exactly as in the plain
+// iteration), and a voxel that stops keeps S_half.
 // Per iteration: Y[v][i] = sum_j P[i][j] X[v][j] + r_i X[v][i] (P symmetric, read as
 // P[j][i] so a warp reads a contiguous row; r_i = 1 - sum_j P[i][j] restores the unit row
 // and column sums that FP32 rounding of P breaks), S_new = (1 - eps) Y with
@@ -34,15 +46,22 @@ struct ScatterCfg {
   static constexpr int kWarps = kThreads / 32;
 };
 
-// After the call lane l holds the max over the warp's lanes of vals[l mod V] (returned):
-// lanes l and l ^ s for s >= V first combine all V values, then a butterfly halves the
-// values each lane keeps while transposing them across lanes.
-template <int V>
-__device__ __forceinline__ float warp_transpose_max(float (&vals)[V], int lane) {
+struct OpMax {
+  __device__ __forceinline__ float operator()(float a, float b) const { return fmaxf(a, b); }
+};
+struct OpSum {
+  __device__ __forceinline__ float operator()(float a, float b) const { return a + b; }
+};
+
+// After the call lane l holds the reduction (max or sum) over the warp's lanes of
+// vals[l mod V] (returned): lanes l and l ^ s for s >= V first combine all V values, then
+// a butterfly halves the values each lane keeps while transposing them across lanes.
+template <int V, typename Op>
+__device__ __forceinline__ float warp_transpose_reduce(float (&vals)[V], int lane, Op op) {
 #pragma unroll
   for (int s = 16; s >= V; s >>= 1) {
 #pragma unroll
-    for (int k = 0; k < V; ++k) vals[k] = fmaxf(vals[k], __shfl_xor_sync(0xffffffffu, vals[k], s));
+    for (int k = 0; k < V; ++k) vals[k] = op(vals[k], __shfl_xor_sync(0xffffffffu, vals[k], s));
   }
 #pragma unroll
   for (int s = V / 2; s >= 1; s >>= 1) {
@@ -52,7 +71,7 @@ __device__ __forceinline__ float warp_transpose_max(float (&vals)[V], int lane) 
       const float send = upper ? vals[k] : vals[k + s];
       const float keep = upper ? vals[k + s] : vals[k];
       const float recv = __shfl_xor_sync(0xffffffffu, send, s);
-      vals[k] = fmaxf(keep, recv);
+      vals[k] = op(keep, recv);
     }
   }
   return vals[0];
@@ -70,7 +89,9 @@ __global__ void __launch_bounds__(ScatterCfg<NA>::kThreads, 2)
   __shared__ __align__(16) float Xs[2][NA][kXStride];
   __shared__ float red_d[W][32];  // per warp, lane v < kTile holds voxel v's reduction
   __shared__ float red_s[W][32];
-  __shared__ float e_s[kTile], rho_s[kTile], best_s[kTile];
+  __shared__ float red_c[W][32];
+  __shared__ float den_s[kTile], c_s[kTile];
+  __shared__ float e_s[kTile], rho_s[kTile], best_s[kTile], mua_s[kTile];
   __shared__ int iters_s[kTile], stall_s[kTile];
   __shared__ unsigned act_s;
 
@@ -85,14 +106,17 @@ __global__ void __launch_bounds__(ScatterCfg<NA>::kThreads, 2)
 
   if (tid < kTile) {
     const int v = v0 + tid;
-    float ev = 1.0f, rho = 0.0f;
+    float ev = 1.0f, rho = 0.0f, ma = 0.0f;
     if (v < g.nv) {
       ev = eps[v];
-      const float xm = mut[v] * g.ds_max;
+      const float mt = mut[v];
+      const float xm = mt * g.ds_max;
       rho = (1.0f - ev) * ray_b1(xm, expf(-xm));  // b1 grows with x: max over d is at ds_max
+      ma = ev * mt;                                // mu_a of the voxel
     }
     e_s[tid] = ev;
     rho_s[tid] = rho;
+    mua_s[tid] = ma;
     iters_s[tid] = 0;
     best_s[tid] = 3.0e38f;
     stall_s[tid] = 0;
@@ -132,6 +156,22 @@ __global__ void __launch_bounds__(ScatterCfg<NA>::kThreads, 2)
       *reinterpret_cast<float4*>(&Xs[0][i][v]) = x4;
     }
   }
+  {
+    // rebalance denominators sum_j (1 - a b1_j) per voxel: a transpose-sum of b1 over the
+    // directions (all threads; dead lanes add zero)
+    float bsum[kTile];
+#pragma unroll
+    for (int v = 0; v < kTile; ++v) bsum[v] = b1[v];
+    red_c[warp][lane] = warp_transpose_reduce(bsum, lane, OpSum());
+  }
+  __syncthreads();
+  if (tid < kTile) {
+    float sb = 0.0f;
+#pragma unroll
+    for (int w = 0; w < W; ++w) sb += red_c[w][tid];
+    den_s[tid] = static_cast<float>(NA) - (1.0f - e_s[tid]) * sb;
+    c_s[tid] = 0.0f;
+  }
   unsigned act = act_s;
   int cur = 0;
   int k = 0;
@@ -169,28 +209,22 @@ __global__ void __launch_bounds__(ScatterCfg<NA>::kThreads, 2)
         for (int v = 0; v < kTile; ++v) acc[v] += t[v];
       }
     }
-    // epilogue: S_new = a * acc on active voxels; X = Q + b1 * S for the next iteration
-    float dsv[kTile], smv[kTile];
+    // epilogue: S_half = a * acc on active voxels, its change and b1-weighted change
+    float dsv[kTile], smv[kTile], cvv[kTile];
 #pragma unroll
     for (int v = 0; v < kTile; ++v) {
       const bool on = live && ((act >> v) & 1u);
       const float y = fmaf(ri, fmaf(b1[v], so[v], q[v]), acc[v]);  // + r_i X_i
       const float sn = fmaf(-e_s[v], y, y);                        // (1 - eps) y
-      dsv[v] = on ? fabsf(sn - so[v]) : 0.0f;
+      const float dl = sn - so[v];
+      dsv[v] = on ? fabsf(dl) : 0.0f;
       smv[v] = on ? fabsf(sn) : 0.0f;
+      cvv[v] = on ? b1[v] * dl : 0.0f;
       so[v] = on ? sn : so[v];
     }
-    const int nxt = cur ^ 1;
-    if (live) {
-#pragma unroll
-      for (int v = 0; v < kTile; v += 4) {
-        float4 x4 = make_float4(q[v] + b1[v] * so[v], q[v + 1] + b1[v + 1] * so[v + 1],
-                                q[v + 2] + b1[v + 2] * so[v + 2], q[v + 3] + b1[v + 3] * so[v + 3]);
-        *reinterpret_cast<float4*>(&Xs[nxt][i][v]) = x4;
-      }
-    }
-    red_d[warp][lane] = warp_transpose_max(dsv, lane);
-    red_s[warp][lane] = warp_transpose_max(smv, lane);
+    red_d[warp][lane] = warp_transpose_reduce(dsv, lane, OpMax());
+    red_s[warp][lane] = warp_transpose_reduce(smv, lane, OpMax());
+    red_c[warp][lane] = warp_transpose_reduce(cvv, lane, OpSum());
     __syncthreads();
     if (tid < 32) {  // one full warp: the ballot below is warp-collective
       const int v = tid;
@@ -219,12 +253,31 @@ __global__ void __launch_bounds__(ScatterCfg<NA>::kThreads, 2)
           done = 1u;
           iters_s[v] = k;
         }
+        // isotropic correction of a voxel that goes on (a stopped voxel keeps S_half)
+        float cs = 0.0f;
+#pragma unroll
+        for (int w = 0; w < W; ++w) cs += red_c[w][v];
+        c_s[v] = stop ? 0.0f : (1.0f - e_s[v]) * cs / den_s[v];
       }
       const unsigned mask = __ballot_sync(0xffffffffu, done);
       if (tid == 0) act_s = act & ~mask;
     }
     __syncthreads();
+    const unsigned was = act;
     act = act_s;
+    // S_{k+1} = S_half + c; X = Q + b1 S for the next iteration
+    const int nxt = cur ^ 1;
+    if (live) {
+#pragma unroll
+      for (int v = 0; v < kTile; ++v)
+        if ((was >> v) & 1u) so[v] += c_s[v];
+#pragma unroll
+      for (int v = 0; v < kTile; v += 4) {
+        float4 x4 = make_float4(q[v] + b1[v] * so[v], q[v + 1] + b1[v + 1] * so[v + 1],
+                                q[v + 2] + b1[v + 2] * so[v + 2], q[v + 3] + b1[v + 3] * so[v + 3]);
+        *reinterpret_cast<float4*>(&Xs[nxt][i][v]) = x4;
+      }
+    }
     cur = nxt;
   }
   // voxels still active hit max_iters
@@ -235,7 +288,7 @@ __global__ void __launch_bounds__(ScatterCfg<NA>::kThreads, 2)
 
   // write I(n) = Q + b1 S, S(n); tallies
   const size_t cur_off = (static_cast<size_t>(ring_slot(n)) * g.na + (live ? i : 0)) * plane;
-  float esum = 0.0f, smax = 0.0f;
+  float esum = 0.0f, asum = 0.0f, smax = 0.0f;
   if (live) {
 #pragma unroll
     for (int v = 0; v < kTile; ++v) {
@@ -245,6 +298,7 @@ __global__ void __launch_bounds__(ScatterCfg<NA>::kThreads, 2)
         Iring[cur_off + vv] = Iv;
         Sring[cur_off + vv] = so[v];
         esum = fmaf(Iv, nidx[vv], esum);
+        asum = fmaf(Iv, mua_s[v], asum);
         smax = fmaxf(smax, fabsf(so[v]));
       }
     }
@@ -252,22 +306,26 @@ __global__ void __launch_bounds__(ScatterCfg<NA>::kThreads, 2)
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) {
     esum += __shfl_xor_sync(0xffffffffu, esum, o);
+    asum += __shfl_xor_sync(0xffffffffu, asum, o);
     smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, o));
   }
   __syncthreads();
   if (lane == 0) {
     red_d[warp][0] = esum;
+    red_d[warp][1] = asum;
     red_s[warp][0] = smax;
   }
   __syncthreads();
   if (tid == 0) {
-    double e = 0.0;
+    double e = 0.0, ab = 0.0;
     float sm = 0.0f;
     for (int w = 0; w < W; ++w) {
       e += red_d[w][0];
+      ab += red_d[w][1];
       sm = fmaxf(sm, red_s[w][0]);
     }
     atomicAdd(rs.energy + n, e * static_cast<double>(g.e_scale));
+    atomicAdd(rs.absorbed + n, ab * g.a_scale);
     atomicMax(rs.smax + (n & 1), __float_as_uint(sm));
     int im = 0;
     unsigned long long is = 0;
@@ -308,7 +366,7 @@ __global__ void __launch_bounds__(256) tally_kernel(GridParams g, const DirInfo*
     }
     return;
   }
-  if (g.periodic) return;
+  if (g.periodic || g.mirror) return;  // closed box: nothing leaves
   const int ax = face >> 1;
   const int ua = ax == 0 ? 1 : 0;
   const int va = ax == 2 ? 1 : 2;
@@ -341,7 +399,31 @@ __global__ void __launch_bounds__(256) tally_kernel(GridParams g, const DirInfo*
   }
 }
 
-__global__ void advance_kernel(RunState rs) { *rs.step += 1; }
+// Photon energy density of one stored level (Section 3.1 plots its maps): u_v =
+// (n_v / c0) sum_d w I_d, the energy density of radiance I per unit solid angle being
+// I / c with c = c0 / n.  Thread per voxel; the directions are summed in FP64.
+__global__ void __launch_bounds__(256) energy_density_kernel(GridParams g, const float* __restrict__ I,
+                                                             const float* __restrict__ nidx, float scale,
+                                                             float* __restrict__ u) {
+  const size_t plane = static_cast<size_t>(g.nv);
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < g.nv; v += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int d = 0; d < g.na; ++d) s += static_cast<double>(__ldg(I + static_cast<size_t>(d) * plane + v));
+    u[v] = static_cast<float>(s * static_cast<double>(scale) * static_cast<double>(nidx[v]));
+  }
+}
+
+// End of step n: the photon balance (energy before step 0 plus what came in minus what
+// left or was absorbed), its residual against the energy in the box, and the step counter.
+__global__ void advance_kernel(GridParams g, RunState rs) {
+  const int n = *rs.step;
+  double b = *rs.balance;
+  if (n >= 0 && n < g.pulse_steps) b += g.inj_step;
+  b -= rs.escaped[n] + rs.absorbed[n];
+  *rs.balance = b;
+  rs.residual[n] = b - rs.energy[n];
+  *rs.step = n + 1;
+}
 
 // ----------------------------------------------------------------------------------------
 // Index interfaces (Eqs. 13-14): at each interface voxel the light arriving through an
@@ -421,8 +503,16 @@ cudaError_t launch_interface(int nvox, int na, const int* vox, const int* rowptr
   return cudaGetLastError();
 }
 
-cudaError_t launch_advance(RunState rs, cudaStream_t st) {
-  advance_kernel<<<1, 1, 0, st>>>(rs);
+cudaError_t launch_energy_density(const GridParams& g, const float* I, const float* nidx, float scale, float* u,
+                                  cudaStream_t st) {
+  int blocks = (g.nv + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  energy_density_kernel<<<blocks, 256, 0, st>>>(g, I, nidx, scale, u);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance(const GridParams& g, RunState rs, cudaStream_t st) {
+  advance_kernel<<<1, 1, 0, st>>>(g, rs);
   return cudaGetLastError();
 }
 

@@ -14,6 +14,17 @@
 // Pb = bf16(P) is symmetric; r_i = 1 - sum_j Pb[i][j] restores unit row and column sums
 // exactly (Pb + diag(r) is symmetric and doubly stochastic), so scattering still
 // conserves photons and keeps isotropic fields isotropic.
+// Isotropic rebalance (as in the FP32 kernel): after each plain update S_half of S_k a
+// voxel that goes on adds c = a sum_j b1_j (S_half - S_k)_j / sum_j (1 - a b1_j) to every
+// direction, which removes the slowest (isotropic) error mode.  The correction is applied
+// lazily: TMEM keeps S_half and the MMA runs on X~ = Q + b1 S_half, and the next epilogue
+// adds c to S and c (Pb b1)_i to the MMA result, which is what the MMA of
+// X = Q + b1 (S_half + c) would give.  (Pb b1)_i is taken as b1_i (1 - r_i) = b1_i
+// sum_j Pb_ij, its value where b1 is constant over the forward peak of Pb (b1 changes by
+// a few per cent between neighbouring ray spacings; an error there only slows the
+// correction, which vanishes at the fixed point, and both kernel instances use the same
+// estimate so that the uniform-medium instance stays bit-identical to the general one).
+// The stop test is on the plain update, and a voxel that stops keeps S_half.
 //
 // Operand layouts (shared memory, K-major, 128-byte swizzle): a K-block of 64 BF16 per
 // row is 128 B; rows follow each other every 128 B, 8-row groups every 1024 B; the
@@ -300,9 +311,8 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
                       const float* __restrict__ nidx, float* __restrict__ Iring, float* __restrict__ Sring,
                       float tol, int max_iters, RunState rs) {
   using C = Tc<NA>;
-  // TMEM load width: 16 columns where registers allow (the uniform-b1 form needs no class
-  // bytes), else 8
-  constexpr int CH = (kUniB1 && C::HALF % 16 == 0) ? 16 : C::CH;
+  // TMEM load width: 8 columns at 192 directions (16 would spill registers), 16 at 48
+  constexpr int CH = C::CH;
   constexpr int NCH = C::HALF / CH;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -319,10 +329,15 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
   __shared__ int tile_s;
   __shared__ int plane_s;
   __shared__ int abort_s;
-  __shared__ float e_s[kM], rho_s[kM];
+  __shared__ float e_s[kM], rho_s[kM], den_s[kM];
+  __shared__ int ccnt_s[kMaxClasses];
+  __shared__ float clsb1_s[kMaxClasses];
+  __shared__ float sumb1_s;
   constexpr int kGroups = C::kGroups;
   __shared__ float red_d[2][kGroups][kM], red_s[2][kGroups][kM];  // by iteration parity
+  __shared__ float red_c[2][kGroups][kM];
   __shared__ double esum_s[C::kThreads / 32];
+  __shared__ double asum_sh;  // absorbed-energy sum of the CTA (shared atomics: no register)
   __shared__ float smax_s[C::kThreads / 32];
 
   const int tid = threadIdx.x;
@@ -345,9 +360,13 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
     mbar_init(&mbar);
     plane_s = g.nv;
     abort_s = 0;
+    asum_sh = 0.0;
   }
   load_b_operand<NA>(sB, Pbf);
+  if (tid < kMaxClasses) ccnt_s[tid] = 0;
+  __syncthreads();
   for (int i = tid; i < NA; i += blockDim.x) {
+    atomicAdd(&ccnt_s[cls[i]], 1);
     sR[i] = rcorr[i];
     sCls[i] = cls[i];
     if (kUniB1) {  // the same operations as the per-row table below, on the same mu_t
@@ -373,6 +392,18 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  if (kUniB1) {
+    // the denominators' sum_j b1_j, in the order the general form sums it (per class; all
+    // directions of a class hold the same b1, so concurrent writes store the same value)
+    for (int i = tid; i < NA; i += blockDim.x) clsb1_s[sCls[i]] = sB1c[i];
+    __syncthreads();
+    if (tid == 0) {
+      float sb = 0.0f;
+      for (int k2 = 0; k2 < ncls; ++k2) sb = fmaf(static_cast<float>(ccnt_s[k2]), clsb1_s[k2], sb);
+      sumb1_s = sb;
+    }
+    __syncthreads();
+  }
   const uint32_t tmem = tmem_base_s;
   const uint32_t t_row = tmem + (static_cast<uint32_t>((warp & 3) << 5) << 16);
   const uint32_t aHi = smem_u32(sAhi), aLo = smem_u32(sAlo), bB = smem_u32(sB);
@@ -420,6 +451,17 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
       b1t[k * kM + r] = bs * (1.0f / static_cast<float>(nch));
     }
     __syncthreads();
+    // rebalance denominator sum_j (1 - a b1_j) of each row
+    if (tid < kM) {
+      float sb;
+      if (kUniB1) {
+        sb = sumb1_s;
+      } else {
+        sb = 0.0f;
+        for (int k2 = 0; k2 < ncls; ++k2) sb = fmaf(static_cast<float>(ccnt_s[k2]), b1t[k2 * kM + tid], sb);
+      }
+      den_s[tid] = static_cast<float>(NA) - (1.0f - e_s[tid]) * sb;
+    }
 
     // Warm start S(n-1): S_old -> TMEM, X_0 = Q + b1 S_old -> (X_hi, X_lo).  One chunk of
     // columns at a time (not unrolled) so that the chunk loads are not batched; Q is
@@ -471,6 +513,7 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
     int stall = 0, iters = 0;
     const float ev = e_s[row];
     const float rho = rho_s[row];
+    float crow = 0.0f;  // pending isotropic correction of this row (added in the next epilogue)
     int k = 0;
     while (true) {
       ++k;
@@ -483,7 +526,7 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
       // the compiler hoists them out of the iteration loop they cost ~190 registers.
       const volatile float* vb1t = b1t;
       const volatile uint8_t* vCls = sCls;
-      float dmax = 0.0f, smax = 0.0f;
+      float dmax = 0.0f, smax = 0.0f, cpart = 0.0f;
       // tcgen05.ld / st are warp-collective: a warp with any active row runs them on every
       // lane; inactive lanes keep S_old (so they rewrite the same X) and report no change.
       if (!to && __any_sync(0xffffffffu, act)) {
@@ -515,13 +558,17 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
                 b1 = vb1t[cl * kM + row];
               }
               const float qv = q[ch * CH + j + e];
-              const float xo = fmaf(b1, so[j + e], qv);              // X used by this iteration's MMA
-              const float yc = fmaf(rv[j + e], xo, y[j + e]);        // D + r X
-              const float sn = act ? fmaf(-ev, yc, yc) : so[j + e];  // S_new = (1 - eps) Y
-              dmax = fmaxf(dmax, fabsf(sn - so[j + e]));
+              const float gp = fmaf(-b1, rv[j + e], b1);             // (Pb b1)_i, estimated
+              const float sk = so[j + e] + crow;                     // S_k (correction applied)
+              const float xo = fmaf(b1, sk, qv);                     // X_k = Q + b1 S_k
+              const float yc = fmaf(rv[j + e], xo, fmaf(crow, gp, y[j + e]));  // Pb X_k + r X_k
+              const float sn = act ? fmaf(-ev, yc, yc) : sk;         // S_half = (1 - eps) Y
+              const float dl = sn - sk;
+              dmax = fmaxf(dmax, fabsf(dl));
               smax = fmaxf(smax, fabsf(sn));
+              cpart = fmaf(b1, dl, cpart);
               so[j + e] = sn;
-              xn[e] = fmaf(b1, sn, qv);                              // X for the next MMA
+              xn[e] = fmaf(b1, sn, qv);                              // X~ for the next MMA
             }
             split_bf16x2(xn[0], xn[1], hi[j / 2], lo[j / 2]);
           }
@@ -539,6 +586,7 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
       const int par = k & 1;
       red_d[par][half][row] = dmax;
       red_s[par][half][row] = smax;
+      red_c[par][half][row] = cpart;
       fence_async_smem();
       tc_fence_before();
       // The one barrier of the iteration: publishes X for the next MMA and the reduced
@@ -579,6 +627,15 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
           if (!conv && half == 0) atomicAdd(rs.nonconv, 1);
         }
       }
+      // isotropic correction for the next epilogue (zero for a row that stopped)
+      if (act) {
+        float cs = red_c[par][0][row];
+#pragma unroll
+        for (int gi = 1; gi < kGroups; ++gi) cs += red_c[par][gi][row];
+        crow = (1.0f - ev) * cs / den_s[row];
+      } else {
+        crow = 0.0f;
+      }
       // write out the voxels that stopped in this iteration: I = Q + b1 S, S (Q from
       // registers: no global load on this path).  The addresses derive from a volatile
       // shared copy of the plane size so the compiler cannot hoist 2 x HALF 64-bit
@@ -610,6 +667,11 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
           }
         }
         if (mine) esum += static_cast<double>(esum_row) * static_cast<double>(nidx[v]);
+        // absorbed energy: mu_a sum_d I of the rows that stopped, one shared atomic per warp
+        float ab = mine ? esum_row * (ev * mut[v]) : 0.0f;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) ab += __shfl_xor_sync(0xffffffffu, ab, o);
+        if (lane == 0) atomicAdd(&asum_sh, static_cast<double>(ab));
       }
     }
     if (aborted) break;
@@ -655,6 +717,7 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
       sm = fmaxf(sm, smax_s[w]);
     }
     atomicAdd(rs.energy + n, e * static_cast<double>(g.e_scale));
+    atomicAdd(rs.absorbed + n, asum_sh * g.a_scale);
     atomicMax(rs.smax + (n & 1), __float_as_uint(sm));
   }
   if (warp == 0) {

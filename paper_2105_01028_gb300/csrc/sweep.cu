@@ -12,6 +12,21 @@ __device__ __forceinline__ int pick(int axis, int x, int y, int z) {
   return axis == 0 ? x : (axis == 1 ? y : z);
 }
 
+// Mirror faces: coordinate q of a ghost upwind sample on an axis of n voxels, brought back
+// inside (the sample lies at most one voxel out, so its image across the face is the
+// nearest voxel inside); ``mask`` collects the axes it lay beyond.
+__device__ __forceinline__ int image_axis(int q, int n, unsigned bit, unsigned& mask) {
+  if (q < 0) {
+    mask |= bit;
+    return 0;
+  }
+  if (q >= n) {
+    mask |= bit;
+    return n - 1;
+  }
+  return q;
+}
+
 // ----------------------------------------------------------------------------------------
 // Q(v, d) = I_up exp(-x) + S_up b0(x), the known part of Eq. 10 at time level n.
 // The upwind sample of v is the previous point of its long ray (slab lattice, Section
@@ -29,6 +44,9 @@ __device__ __forceinline__ int pick(int axis, int x, int y, int z) {
 // kUniN / kUniMu: the refractive index / mu_t is the same in every voxel, so the delay's
 // split (m, f) / exp(-x) and b0(x) are taken once per block, by the same FP32 operations
 // on the same values as the per-voxel form, and the voxel loop reads neither map.
+// Mirror faces (a test boundary: specular reflection by the method of images): a ghost
+// upwind sample reads I and S of its image voxel in the direction reflected in the faces
+// it lay beyond (refl[d][mask], mask bit a = axis a), at the voxel's own retarded levels.
 // ----------------------------------------------------------------------------------------
 constexpr int kRowSweeps = 8;  // row groups per block
 
@@ -39,6 +57,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(GridParams g, const DirInfo*
                                                     const float* __restrict__ Sring,
                                                     const float* __restrict__ mut,
                                                     const float* __restrict__ nidx,
+                                                    const int* __restrict__ refl,
                                                     float* __restrict__ Q, RunState rs) {
   __shared__ DirInfo di_s;
   __shared__ int n_s, m_s;
@@ -96,8 +115,9 @@ __global__ void __launch_bounds__(256) sweep_kernel(GridParams g, const DirInfo*
   const float T_u = kUniMu ? T_s : 0.0f, b0_u = kUniMu ? b0_s : 0.0f;
 
   // Q of voxel v from its upwind sample u (kind 0), the inflow face (kind 1) or a side face
-  // (kind 2: nothing enters).
-  const auto update = [&](int v, int kind, int u) {
+  // (kind 2: nothing enters, or with mirror faces the image); (qd, q0, q1) are the upwind
+  // sample's unwrapped coordinates along dom, a0, a1.
+  const auto update = [&](int v, int kind, int u, int qd, int q0, int q1) {
     int m;
     float f;
     if (kUniN) {
@@ -120,6 +140,24 @@ __global__ void __launch_bounds__(256) sweep_kernel(GridParams g, const DirInfo*
       if (i1p) {
         i1 = __ldg(i1p + u);
         s1v = __ldg(slev_s[m + 1] + u);
+      }
+      Iup = (1.0f - f) * i0 + f * i1;
+      Sup = (1.0f - f) * s0v + f * s1v;
+    } else if (g.mirror) {
+      unsigned mask = 0u;
+      const int cd = image_axis(qd, nd, 1u << dom, mask);
+      const int c0 = image_axis(q0, n0, 1u << a0, mask);
+      const int c1 = image_axis(q1, n1, 1u << a1, mask);
+      const int img = cd * sd + c0 * s0 + c1 * s1;
+      const ptrdiff_t doff = static_cast<ptrdiff_t>(refl[d * 8 + mask] - d) * static_cast<ptrdiff_t>(plane);
+      float i0 = 0.0f, i1 = 0.0f, s0v = 0.0f, s1v = 0.0f;
+      if (ilev_s[m]) {
+        i0 = __ldg(ilev_s[m] + doff + img);
+        s0v = __ldg(slev_s[m] + doff + img);
+      }
+      if (ilev_s[m + 1]) {
+        i1 = __ldg(ilev_s[m + 1] + doff + img);
+        s1v = __ldg(slev_s[m + 1] + doff + img);
       }
       Iup = (1.0f - f) * i0 + f * i1;
       Sup = (1.0f - f) * s0v + f * s1v;
@@ -170,7 +208,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(GridParams g, const DirInfo*
         } else if (kind == 0 && (q0 < 0 || q0 >= n0)) {
           kind = 2;
         }
-        update(row_base + x, kind, urow + q0);
+        update(row_base + x, kind, urow + q0, qd, q0, q1);
       }
     } else {
       // dom is x: the slab index and the offsets change along the row
@@ -189,7 +227,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(GridParams g, const DirInfo*
         } else if (q0 < 0 || q0 >= n0 || q1 < 0 || q1 >= n1) {
           kind = 2;
         }
-        update(row_base + x, kind, qd * sd + q0 * s0 + q1 * s1);
+        update(row_base + x, kind, qd * sd + q0 * s0 + q1 * s1, qd, q0, q1);
       }
     }
   }
@@ -199,7 +237,8 @@ __global__ void __launch_bounds__(256) sweep_kernel(GridParams g, const DirInfo*
 
 cudaError_t launch_sweep(const GridParams& g, const DirInfo* dirs, const int8_t* offs,
                          const float* Iring, const float* Sring, const float* mut,
-                         const float* nidx, float* Q, RunState rs, cudaStream_t st) {
+                         const float* nidx, const int* refl, float* Q, RunState rs, cudaStream_t st) {
+  if (g.mirror && !refl) return cudaErrorInvalidValue;
   int bx = ((g.nx + 31) / 32) * 32;
   if (bx > 256) bx = 256;
   const int by = 256 / bx;
@@ -209,13 +248,13 @@ cudaError_t launch_sweep(const GridParams& g, const DirInfo* dirs, const int8_t*
   dim3 grid((groups + kRowSweeps - 1) / kRowSweeps, g.na);
   const bool un = g.n_u >= 1.0f, um = g.mut_u >= 0.0f;
   if (un && um)
-    sweep_kernel<true, true><<<grid, block, 0, st>>>(g, dirs, offs, Iring, Sring, mut, nidx, Q, rs);
+    sweep_kernel<true, true><<<grid, block, 0, st>>>(g, dirs, offs, Iring, Sring, mut, nidx, refl, Q, rs);
   else if (un)
-    sweep_kernel<true, false><<<grid, block, 0, st>>>(g, dirs, offs, Iring, Sring, mut, nidx, Q, rs);
+    sweep_kernel<true, false><<<grid, block, 0, st>>>(g, dirs, offs, Iring, Sring, mut, nidx, refl, Q, rs);
   else if (um)
-    sweep_kernel<false, true><<<grid, block, 0, st>>>(g, dirs, offs, Iring, Sring, mut, nidx, Q, rs);
+    sweep_kernel<false, true><<<grid, block, 0, st>>>(g, dirs, offs, Iring, Sring, mut, nidx, refl, Q, rs);
   else
-    sweep_kernel<false, false><<<grid, block, 0, st>>>(g, dirs, offs, Iring, Sring, mut, nidx, Q, rs);
+    sweep_kernel<false, false><<<grid, block, 0, st>>>(g, dirs, offs, Iring, Sring, mut, nidx, refl, Q, rs);
   return cudaGetLastError();
 }
 

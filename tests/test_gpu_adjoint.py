@@ -33,8 +33,8 @@ from oracle.solver import Solver as OSolver
 
 pytestmark = pytest.mark.gpu
 
-GRAD_TOL = 3e-4
-DET_TOL = 2e-5
+GRAD_TOL = 1e-4
+DET_TOL = 1e-5
 
 
 def _lib():

@@ -1,23 +1,15 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle.
 
-Tolerances (FP32 mode), derived from the arithmetic.  The oracle runs its source
-iteration to 1e-10 (the fixed point to FP64 accuracy).  The GPU runs with tol = 1e-7 and
-stops at the noise floor of its FP32 angular sums (stall exit): the iterate then sits
-within ~rho/(1-rho) x (sum rounding, ~1e-7) of the fixed point, and at the small
-workload's optics rho/(1-rho) ~ 13.  Transport conserves photons, so these per-step
-errors add up over the run.  A float32 emulation of the oracle with the kernel's
-summation order reproduces the GPU (detector curves 7e-6 of peak, single field values
-1.2e-4 of the field peak after 100 steps; even FP64 stopped at tol 1e-6 is 2.3e-5 off
-the converged field).  The GPU measures 1.4e-5 on those detector curves and the energy
-tally, and 1.05e-5 on the heterogeneous workload: the residual is the FP32 rounding of
-the angular sums divided by (1 - rho) and summed over conservative transport; removing
-it would need compensated sums (about +50% of the FP32 path's work).  Bars: detector
-curves and energy tallies 1e-5 of their peak, 2e-5 on the two slow-converging workloads
-(small: rho ~ 0.93; heterogeneous); ragged-grid fields 1e-5 and heterogeneous fields
-2e-5 of their peak; the small workload's full fields 2e-4 of their peak; detector bins
-above 1e-6 of the peak 5e-4 each.  At the workloads' own tol = 1e-6 both sides stop
-one-sidedly short of the fixed point, so that case is compared with the oracle at the
-same tol and a bar of 3e-5.
+Tolerances (FP32 mode): 1e-5 of the peak for fields, detector curves and energy tallies,
+and 5e-4 per detector bin above 1e-6 of the peak.  The oracle runs its source iteration
+to 1e-10 (the fixed point to FP64 accuracy); the GPU runs with tol = 1e-7 (or the
+workloads' 1e-6) and stops at the noise floor of its FP32 angular sums at the latest
+(stall exit).  With the isotropic rebalance after every plain update (see the FP32
+kernel) the slowest error mode no longer leaves the stopped iterate ~1/(1 - a b1) ~ 14
+noise units short of the fixed point, always on the same side, so the per-step error
+stays at the FP32 rounding of the sums and does not build up over the photon-conserving
+transport: the small workload measures ~1e-6 on detector curves, energy and fields after
+100 steps (without the rebalance: 1.4e-5 on detector curves and 1.2e-4 on fields).
 """
 import numpy as np
 import pytest
@@ -27,8 +19,6 @@ import workloads as W
 pytestmark = pytest.mark.gpu
 
 FP32_TOL = 1e-5
-FIELD_TOL_SLOW = 2e-4  # full fields of the rho ~ 0.93 small workload (see module docstring)
-DET_TOL_SLOW = 2e-5    # detector curves of the slow-converging workloads (see module docstring)
 
 
 def _gpu():
@@ -80,21 +70,21 @@ def small_run():
 
 def test_small_config_detectors(small_run):
     out, ref = small_run
-    _check_detectors(out["det"], ref.det, DET_TOL_SLOW)
+    _check_detectors(out["det"], ref.det, FP32_TOL)
 
 
 def test_small_config_energy_tallies(small_run):
     out, ref = small_run
     N, esc = out["energy"]
-    assert _rel_peak(N, np.array(ref.energy)) <= DET_TOL_SLOW
-    assert _rel_peak(esc, np.array(ref.escaped)) <= DET_TOL_SLOW
+    assert _rel_peak(N, np.array(ref.energy)) <= FP32_TOL
+    assert _rel_peak(esc, np.array(ref.escaped)) <= FP32_TOL
 
 
 def test_small_config_fields_elementwise(small_run):
     out, ref = small_run
-    assert _rel_peak(out["I"], ref.level("I")) <= FIELD_TOL_SLOW
-    assert _rel_peak(out["S"], ref.level("S")) <= FIELD_TOL_SLOW
-    assert _rel_peak(out["I1"], ref.level("I", back=1)) <= FIELD_TOL_SLOW
+    assert _rel_peak(out["I"], ref.level("I")) <= FP32_TOL
+    assert _rel_peak(out["S"], ref.level("S")) <= FP32_TOL
+    assert _rel_peak(out["I1"], ref.level("I", back=1)) <= FP32_TOL
 
 
 def test_small_config_iteration_counts_plausible(small_run):
@@ -104,15 +94,17 @@ def test_small_config_iteration_counts_plausible(small_run):
     assert np.all(out["iters"][2:] <= np.array(ref.iters_max)[2:] + 5)
 
 
-def test_small_config_at_workload_tolerance():
-    """At the workload's tol = 1e-6, against the oracle at the same tolerance."""
+def test_small_config_at_workload_tolerance(small_run):
+    """At the workload's own tol = 1e-6 the GPU still lands within the FP32 bar of the
+    converged solution (the stop rule bounds the error of each step's iterate by tol, and
+    the rebalance keeps that error from being one-sided)."""
     T = _gpu()
+    _, ref = small_run
     prob = W.config_small(steps=100, tol=1e-6)
     fwd = T.Forward(prob)
     fwd.step(100)
-    ref = _oracle(prob, 100, tol=1e-6)
-    _check_detectors(fwd.detectors(), ref.det, 3e-5)
-    assert _rel_peak(fwd.field(T.FIELD_I), ref.level("I")) <= FIELD_TOL_SLOW
+    _check_detectors(fwd.detectors(), ref.det, FP32_TOL)
+    assert _rel_peak(fwd.field(T.FIELD_I), ref.level("I")) <= FP32_TOL
     fwd.close()
 
 
@@ -147,8 +139,8 @@ def test_heterogeneous_optics_small():
     fwd = T.Forward(prob)
     fwd.step(30)
     ref = _oracle(prob, 30)
-    assert _rel_peak(fwd.field(T.FIELD_I), ref.level("I")) <= 2 * FP32_TOL
-    _check_detectors(fwd.detectors(), ref.det, DET_TOL_SLOW)
+    assert _rel_peak(fwd.field(T.FIELD_I), ref.level("I")) <= FP32_TOL
+    _check_detectors(fwd.detectors(), ref.det, FP32_TOL)
     fwd.close()
 
 
@@ -279,8 +271,8 @@ def test_heterogeneous_with_fresnel_interfaces(precision):
     ref = _oracle(prob, 40)
     assert len(ref.m.interfaces) == fwd.interface_count()
     if precision == "fp32":
-        assert _rel_peak(fwd.field(T.FIELD_I), ref.level("I")) <= 2 * FP32_TOL
-        _check_detectors(fwd.detectors(), ref.det, DET_TOL_SLOW)
+        assert _rel_peak(fwd.field(T.FIELD_I), ref.level("I")) <= FP32_TOL
+        _check_detectors(fwd.detectors(), ref.det, FP32_TOL)
     else:
         got, want = fwd.detectors(), ref.det
         assert np.linalg.norm(got - want) <= 1e-3 * np.linalg.norm(want)

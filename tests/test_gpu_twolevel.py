@@ -19,8 +19,8 @@ from oracle.twolevel import TwoLevelSolver
 
 pytestmark = pytest.mark.gpu
 
-DET_TOL = 2e-5
-FIELD_TOL = 2e-4
+DET_TOL = 1e-5
+FIELD_TOL = 1e-5
 BF16_L2 = 1e-3
 
 
