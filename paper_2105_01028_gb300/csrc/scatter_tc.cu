@@ -30,7 +30,9 @@
 // row is 128 B; rows follow each other every 128 B, 8-row groups every 1024 B; the
 // 16-byte chunk c of row r sits at chunk position c ^ (r & 7).  A = X tile (128 rows x
 // K), B = Pb (N_a rows x K), K padded to a multiple of 64 with zeros.
-// TMEM: columns [0, N_a) hold D, columns [SOFF, SOFF + N_a) hold S_old (FP32).
+// TMEM: columns [0, N_a) hold D, columns [SOFF, SOFF + N_a) hold S_old (FP32); at 192
+// directions the 128 columns left over hold two thirds of the tile's Q (read from HBM
+// once per tile), the rest of Q stays in registers.
 // Thread mapping: 16 warps (12 for 48 directions); warp w reads TMEM lanes 32 (w % 4) ..
 // + 31 (one voxel row per thread) and the column group w / 4 (a quarter / third of the
 // directions).
@@ -68,12 +70,17 @@ struct Tc {
   static constexpr int kGroups = TcThreads<NA>::kGroups;
   static constexpr int kThreads = TcThreads<NA>::kThreads;
   static constexpr int HALF = NA / kGroups;        // columns per thread
-  static constexpr int CH = (HALF % 16 == 0 && NA < 192) ? 16 : 8;  // TMEM load width
+  static constexpr int CH = (HALF % 16 == 0 && NA < 192) ? 16 : 8;  // TMEM load width (8 is faster at 192)
   static constexpr int NCH = HALF / CH;
   static_assert(HALF % 8 == 0, "column group must be a whole number of 16-byte chunks");
   static constexpr int POW2 = NA <= 64 ? 64 : (NA <= 128 ? 128 : 256);
   static constexpr int TCOLS = 2 * POW2;           // TMEM allocation (power of 2 >= 32)
   static constexpr int SOFF = POW2;                // S_old column offset
+  // Q of the tile: at 192 directions 32 of each thread's 48 columns live in the TMEM
+  // columns D and S leave free ([192, 256) and [448, 512), 32 per column group) and 16 in
+  // registers, which leaves the registers for 16-column chunks; at 48 all in registers.
+  static constexpr int QT = (NA == 192) ? 32 : 0;  // Q columns per thread kept in TMEM
+  static constexpr int QR = HALF - QT;             // Q columns per thread kept in registers
   static constexpr int B_BYTES = KB * NA * 128;
   static constexpr int A_BYTES = KB * kM * 128;
   static constexpr int OFF_B = 0;
@@ -311,9 +318,10 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
                       const float* __restrict__ nidx, float* __restrict__ Iring, float* __restrict__ Sring,
                       float tol, int max_iters, RunState rs) {
   using C = Tc<NA>;
-  // TMEM load width: 8 columns at 192 directions (16 would spill registers), 16 at 48
-  constexpr int CH = C::CH;
+  constexpr int CH = C::CH;  // TMEM load width
   constexpr int NCH = C::HALF / CH;
+  constexpr int NCT = C::QT / CH;  // chunks whose Q lives in TMEM (the first NCT of a thread)
+  static_assert(C::QT % CH == 0 && C::QR % CH == 0, "Q split must be whole chunks");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sB = smem + C::OFF_B;
@@ -406,13 +414,15 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
   }
   const uint32_t tmem = tmem_base_s;
   const uint32_t t_row = tmem + (static_cast<uint32_t>((warp & 3) << 5) << 16);
+  // this thread's Q columns in TMEM (column group h: 192 + 32 h for h < 2, 448 + 32 (h - 2))
+  const uint32_t t_q = t_row + static_cast<uint32_t>(half < 2 ? NA + C::QT * half : C::SOFF + NA + C::QT * (half - 2));
   const uint32_t aHi = smem_u32(sAhi), aLo = smem_u32(sAlo), bB = smem_u32(sB);
   uint32_t phase = 0;
   bool aborted = false;
   double esum = 0.0;
   float smax_loc = 0.0f;
 
-  float q[C::HALF];
+  float qr[C::QR > 0 ? C::QR : 1];  // Q of the thread's last QR columns
 
   while (true) {
     if (tid == 0) tile_s = atomicAdd(rs.tile_ctr + (n & 1), 1);
@@ -463,26 +473,23 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
       den_s[tid] = static_cast<float>(NA) - (1.0f - e_s[tid]) * sb;
     }
 
-    // Warm start S(n-1): S_old -> TMEM, X_0 = Q + b1 S_old -> (X_hi, X_lo).  One chunk of
-    // columns at a time (not unrolled) so that the chunk loads are not batched; Q is
-    // re-read here and kept in registers only for the iteration loop below.
-#pragma unroll 1
-    for (int ch = 0; ch < NCH; ++ch) {
+    // Warm start S(n-1): S_old -> TMEM, X_0 = Q + b1 S_old -> (X_hi, X_lo), and Q (read
+    // once) -> TMEM or registers.  The TMEM chunks go one at a time (not unrolled) so that
+    // their loads are not batched.
+    const auto warm = [&](int ch, float (&qc)[CH]) {
       const int c0 = cb + ch * CH;
       float so[CH];
       uint32_t hi[CH / 2], lo[CH / 2];
 #pragma unroll
-      for (int j = 0; j < CH; ++j)
+      for (int j = 0; j < CH; ++j) {
         so[j] = (vin && has_prev) ? Sring[prev_base + static_cast<size_t>(c0 + j) * plane + v] : 0.0f;
+        qc[j] = vin ? __ldg(Q + static_cast<size_t>(c0 + j) * plane + v) : 0.0f;
+      }
 #pragma unroll
       for (int j = 0; j < CH; j += 2) {
-        const float q0 = vin ? __ldg(Q + static_cast<size_t>(c0 + j) * plane + v) : 0.0f;
-        const float q1 = vin ? __ldg(Q + static_cast<size_t>(c0 + j + 1) * plane + v) : 0.0f;
         const float b1a = kUniB1 ? sB1c[c0 + j] : b1t[sCls[c0 + j] * kM + row];
         const float b1b = kUniB1 ? sB1c[c0 + j + 1] : b1t[sCls[c0 + j + 1] * kM + row];
-        const float x0 = q0 + b1a * so[j];
-        const float x1 = q1 + b1b * so[j + 1];
-        split_bf16x2(x0, x1, hi[j / 2], lo[j / 2]);
+        split_bf16x2(fmaf(b1a, so[j], qc[j]), fmaf(b1b, so[j + 1], qc[j + 1]), hi[j / 2], lo[j / 2]);
       }
       tmem_st<CH>(t_row + C::SOFF + c0, so);
 #pragma unroll
@@ -492,10 +499,20 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
         *reinterpret_cast<uint4*>(sAlo + sw128_chunk_off(kM, row, c0 + j)) =
             make_uint4(lo[j / 2], lo[j / 2 + 1], lo[j / 2 + 2], lo[j / 2 + 3]);
       }
+    };
+#pragma unroll 1
+    for (int ch = 0; ch < NCT; ++ch) {
+      float qc[CH];
+      warm(ch, qc);
+      tmem_st<CH>(t_q + ch * CH, qc);
     }
 #pragma unroll
-    for (int c = 0; c < C::HALF; ++c)
-      q[c] = vin ? __ldg(Q + static_cast<size_t>(cb + c) * plane + v) : 0.0f;
+    for (int ch = NCT; ch < NCH; ++ch) {
+      float qc[CH];
+      warm(ch, qc);
+#pragma unroll
+      for (int j = 0; j < CH; ++j) qr[(ch - NCT) * CH + j] = qc[j];
+    }
     tmem_wait_st();
     fence_async_smem();
     tc_fence_before();
@@ -533,53 +550,58 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
 #pragma unroll
         for (int ch = 0; ch < NCH; ++ch) {
           const int c0 = cb + ch * CH;
-          float y[CH], so[CH];
+          float y[CH], so[CH], qv_[CH];
           tmem_ld<CH>(t_row + c0, y);
           tmem_ld<CH>(t_row + C::SOFF + c0, so);
+          if (ch < NCT) tmem_ld<CH>(t_q + ch * CH, qv_);
           tmem_wait_ld();
-          uint32_t hi[CH / 2], lo[CH / 2];
-          float rv[CH], bv[CH];
-          uint32_t cv[CH / 4];
-          lds_vec<CH>(sR + c0, rv);
-          if (kUniB1)
-            lds_vec<CH>(sB1c + c0, bv);
-          else
-            lds_bytes<CH>(sCls + c0, cv);
+          if (ch >= NCT) {
 #pragma unroll
-          for (int j = 0; j < CH; j += 2) {
-            float xn[2];
+            for (int j = 0; j < CH; ++j) qv_[j] = qr[(ch - NCT) * CH + j];
+          }
+          // per 8 columns: the tables, the update and the 16-byte X stores
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
-              float b1;
-              if (kUniB1) {
-                b1 = bv[j + e];
-              } else {
-                const int cl = static_cast<int>((cv[(j + e) >> 2] >> (8 * ((j + e) & 3))) & 0xffu);
-                b1 = vb1t[cl * kM + row];
+          for (int j8 = 0; j8 < CH; j8 += 8) {
+            uint32_t hi[4], lo[4];
+            float rv[8], bv[8];
+            uint32_t cv[2];
+            lds_vec<8>(sR + c0 + j8, rv);
+            if (kUniB1)
+              lds_vec<8>(sB1c + c0 + j8, bv);
+            else
+              lds_bytes<8>(sCls + c0 + j8, cv);
+#pragma unroll
+            for (int jj = 0; jj < 8; jj += 2) {
+              float xn[2];
+#pragma unroll
+              for (int e = 0; e < 2; ++e) {
+                const int j = j8 + jj + e;
+                float b1;
+                if (kUniB1) {
+                  b1 = bv[jj + e];
+                } else {
+                  const int cl = static_cast<int>((cv[(jj + e) >> 2] >> (8 * ((jj + e) & 3))) & 0xffu);
+                  b1 = vb1t[cl * kM + row];
+                }
+                const float qv = qv_[j];
+                const float gp = fmaf(-b1, rv[jj + e], b1);            // (Pb b1)_i, estimated
+                const float sk = so[j] + crow;                         // S_k (correction applied)
+                const float xo = fmaf(b1, sk, qv);                     // X_k = Q + b1 S_k
+                const float yc = fmaf(rv[jj + e], xo, fmaf(crow, gp, y[j]));  // Pb X_k + r X_k
+                const float sn = act ? fmaf(-ev, yc, yc) : sk;         // S_half = (1 - eps) Y
+                const float dl = sn - sk;
+                dmax = fmaxf(dmax, fabsf(dl));
+                smax = fmaxf(smax, fabsf(sn));
+                cpart = fmaf(b1, dl, cpart);
+                so[j] = sn;
+                xn[e] = fmaf(b1, sn, qv);                              // X~ for the next MMA
               }
-              const float qv = q[ch * CH + j + e];
-              const float gp = fmaf(-b1, rv[j + e], b1);             // (Pb b1)_i, estimated
-              const float sk = so[j + e] + crow;                     // S_k (correction applied)
-              const float xo = fmaf(b1, sk, qv);                     // X_k = Q + b1 S_k
-              const float yc = fmaf(rv[j + e], xo, fmaf(crow, gp, y[j + e]));  // Pb X_k + r X_k
-              const float sn = act ? fmaf(-ev, yc, yc) : sk;         // S_half = (1 - eps) Y
-              const float dl = sn - sk;
-              dmax = fmaxf(dmax, fabsf(dl));
-              smax = fmaxf(smax, fabsf(sn));
-              cpart = fmaf(b1, dl, cpart);
-              so[j + e] = sn;
-              xn[e] = fmaf(b1, sn, qv);                              // X~ for the next MMA
+              split_bf16x2(xn[0], xn[1], hi[jj / 2], lo[jj / 2]);
             }
-            split_bf16x2(xn[0], xn[1], hi[j / 2], lo[j / 2]);
+            *reinterpret_cast<uint4*>(sAhi + sw128_chunk_off(kM, row, c0 + j8)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4*>(sAlo + sw128_chunk_off(kM, row, c0 + j8)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
           }
           tmem_st<CH>(t_row + C::SOFF + c0, so);
-#pragma unroll
-          for (int j = 0; j < CH; j += 8) {
-            *reinterpret_cast<uint4*>(sAhi + sw128_chunk_off(kM, row, c0 + j)) =
-                make_uint4(hi[j / 2], hi[j / 2 + 1], hi[j / 2 + 2], hi[j / 2 + 3]);
-            *reinterpret_cast<uint4*>(sAlo + sw128_chunk_off(kM, row, c0 + j)) =
-                make_uint4(lo[j / 2], lo[j / 2 + 1], lo[j / 2 + 2], lo[j / 2 + 3]);
-          }
         }
         tmem_wait_st();
       }
@@ -648,15 +670,20 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
 #pragma unroll
         for (int ch = 0; ch < NCH; ++ch) {
           const int c0 = cb + ch * CH;
-          float so[CH];
+          float so[CH], qv_[CH];
           tmem_ld<CH>(t_row + C::SOFF + c0, so);
+          if (ch < NCT) tmem_ld<CH>(t_q + ch * CH, qv_);
           tmem_wait_ld();
+          if (ch >= NCT) {
+#pragma unroll
+            for (int j = 0; j < CH; ++j) qv_[j] = qr[(ch - NCT) * CH + j];
+          }
 #pragma unroll
           for (int j = 0; j < CH; ++j) {
             if (mine) {
               const float b1 = kUniB1 ? reinterpret_cast<const volatile float*>(sB1c)[c0 + j]
                                       : vb1t[vCls[c0 + j] * kM + row];
-              const float Iv = fmaf(b1, so[j], q[ch * CH + j]);
+              const float Iv = fmaf(b1, so[j], qv_[j]);
               *pI = Iv;
               *pS = so[j];
               esum_row += Iv;
