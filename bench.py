@@ -522,6 +522,7 @@ def measure_window(T, torch, prob, stream, spinup, warmup, steps, what):
     kms = fwd.profile(kp)
     _, k_it_mean = fwd.iterations()
     executed = fwd.executed_iterations()[first:first + steps]
+    kps = fwd.kernels_per_step()
     fwd.close()
     nv = prob["nx"] * prob["ny"] * prob["nz"]
     na = 12 * prob["nside"] ** 2
@@ -532,7 +533,7 @@ def measure_window(T, torch, prob, stream, spinup, warmup, steps, what):
             "iterations": {"mean": float(np.mean(it_mean[first:first + steps])),
                            "max": int(np.max(it_max[first:first + steps])),
                            "executed_per_voxel": float(np.mean(executed))},
-            "status": int(status), "gpu_launches": 4 * steps, "roofline": roof, "kernels": kernels,
+            "status": int(status), "gpu_launches": kps * steps, "roofline": roof, "kernels": kernels,
             "clocks": clk.summary()}
 
 
@@ -560,6 +561,7 @@ def measure_whole_run(T, torch, prob, stream, steps, what, repeats=5):
     fwd.reset()
     kms = fwd.profile(steps)
     _, k_it_mean = fwd.iterations()
+    kps = fwd.kernels_per_step()
     fwd.close()
     nv = prob["nx"] * prob["ny"] * prob["nz"]
     na = 12 * prob["nside"] ** 2
@@ -569,7 +571,7 @@ def measure_whole_run(T, torch, prob, stream, steps, what, repeats=5):
             "ms_per_step": best / steps, "steps": steps,
             "timing": "whole %d-step solve from step 0, best of %d (CUDA events; graph replay)" % (steps, repeats),
             "iterations": {"mean": float(np.mean(it_mean)), "max": int(np.max(it_max))},
-            "status": int(status), "gpu_launches": 4 * steps, "roofline": roof, "kernels": kernels,
+            "status": int(status), "gpu_launches": kps * steps, "roofline": roof, "kernels": kernels,
             "clocks": clk.summary(),
             "l2": "L2-resident (%.1f MB of time-level history): launch- and latency-bound" % (
                 2 * 5 * nv * na * 4 / 1e6)}
@@ -681,6 +683,7 @@ def main():
     k_it_max, k_it_mean = fwd.iterations()
     k_mean = float(np.mean(k_it_mean[-kp:]))
     executed = fwd.executed_iterations()[first:first + args.steps]
+    kps = fwd.kernels_per_step()
     fwd.close()
 
     updates = nv * na * args.steps
@@ -737,7 +740,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if (args.exact or args.precision == "fp32") else "bf16-scatter/f32-sweep",
             "data": "synthetic", "config": workload_config(args),
-            "gpu_launches": (5 if nch > 1 else 4) * args.steps,
+            "gpu_launches": kps * args.steps,
             "iterations": {"mean": float(np.mean(win_mean)), "max": int(np.max(win_max)),
                            "executed_per_voxel": float(np.mean(executed))},
             "status": int(status),

@@ -230,6 +230,10 @@ int trinity_read_field(trinity_ctx* ctx, int what, int back, void* out, size_t b
 /* Steps completed so far. */
 int trinity_steps_done(const trinity_ctx* ctx, int* n);
 
+/* Kernel launches one time step issues with the context's current inputs (sweep or
+ * sweeps, interface split, source iteration, tallies, step counter). */
+int trinity_kernels_per_step(const trinity_ctx* ctx, int* n);
+
 /* Zero the fields, tallies and step counter; keep grid, optics, source and detectors. */
 int trinity_reset(trinity_ctx* ctx);
 

@@ -219,6 +219,12 @@ class Forward:
         return self._check(self.L.trinity_reset(self.h))
 
     # -- outputs
+    def kernels_per_step(self):
+        """Kernel launches of one time step with the current inputs."""
+        n = ctypes.c_int()
+        self._check(self.L.trinity_kernels_per_step(self.h, ctypes.byref(n)))
+        return n.value
+
     def steps_done(self):
         n = ctypes.c_int()
         self._check(self.L.trinity_steps_done(self.h, ctypes.byref(n)))

@@ -66,6 +66,7 @@ SIGNATURES = {
     "trinity_profile_steps": (c_int, [c_void_p, c_int, P_double]),
     "trinity_read_detectors": (c_int, [c_void_p, P_double, c_size_t]),
     "trinity_read_energy": (c_int, [c_void_p, P_double, P_double, P_double, P_double, c_size_t]),
+    "trinity_kernels_per_step": (c_int, [c_void_p, P_int]),
     "trinity_read_iterations": (c_int, [c_void_p, P_int, P_double, c_size_t]),
     "trinity_read_executed_iterations": (c_int, [c_void_p, P_double, c_size_t]),
     "trinity_read_field": (c_int, [c_void_p, c_int, c_int, c_void_p, c_size_t, c_int]),

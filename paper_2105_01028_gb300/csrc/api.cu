@@ -81,6 +81,13 @@ struct trinity_ctx {
 
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
+  // TMA-staged sweep (uniform n, vacuum faces, nx % 4 == 0): tensor maps of the rings and
+  // the directions of each dominant-axis class
+  bool tma = false;
+  SweepMaps maps{};
+  int* d_dlist[3] = {nullptr, nullptr, nullptr};
+  int ndir[3] = {0, 0, 0};
+  int8_t* d_hsh = nullptr;  // per direction: bit 0 / 1 set when its y / z lattice offsets are positive
   GridParams graph_g{}, graph_gs{};  // the parameters the captured kernels were given
 
   // two-level angular grid: S on na_s coarse directions, each the mean of nch children
@@ -518,6 +525,10 @@ int enqueue_transport(trinity_ctx* ctx, const RunState& rs) {
   if (ctx->two_level) {
     CK(launch_sweep2(g, ctx->d_dirs, ctx->d_offs, ctx->d_children, ctx->nch, ctx->na_s, ctx->I, ctx->S,
                      ctx->mut, ctx->nidx, ctx->Q, ctx->Qc, rs, ctx->stream));
+  } else if (ctx->tma && g.n_u >= 1.0f) {
+    const int* dl[3] = {ctx->d_dlist[0], ctx->d_dlist[1], ctx->d_dlist[2]};
+    CK(launch_sweep_tma(g, ctx->d_dirs, dl, ctx->ndir, ctx->d_offs, ctx->d_hsh, ctx->maps, ctx->mut, ctx->Q, rs,
+                        ctx->stream));
   } else {
     CK(launch_sweep(g, ctx->d_dirs, ctx->d_offs, ctx->I, ctx->S, ctx->mut, ctx->nidx, ctx->d_refl, ctx->Q, rs,
                     ctx->stream));
@@ -865,6 +876,28 @@ int trinity_create_grid(const trinity_grid_desc* desc, void* cuda_stream, trinit
         cudaMemcpy(ctx->d_cls_ds, flat.data(), flat.size() * sizeof(float), cudaMemcpyHostToDevice) !=
             cudaSuccess)
       return bail(TRINITY_E_CUDA);
+  }
+  if (!ctx->two_level && sweep_tma_supported(g)) {
+    // directions of each dominant-axis class, for the TMA-staged sweep
+    std::vector<int> cl[3];
+    for (int d = 0; d < g.na; ++d) cl[ctx->lat.dom[d]].push_back(d);
+    bool ok = make_sweep_maps(g, ctx->I, ctx->S, &ctx->maps) == cudaSuccess;
+    for (int c = 0; c < 3 && ok; ++c) {
+      ctx->ndir[c] = static_cast<int>(cl[c].size());
+      ok = dalloc(&ctx->d_dlist[c], cl[c].size()) == cudaSuccess &&
+           (cl[c].empty() || cudaMemcpy(ctx->d_dlist[c], cl[c].data(), cl[c].size() * sizeof(int),
+                                        cudaMemcpyHostToDevice) == cudaSuccess);
+    }
+    // the sign of each transverse lattice offset (all offsets of a direction and axis share it)
+    std::vector<int8_t> hsh(g.na, 0);
+    for (int d = 0; d < g.na; ++d)
+      for (int j = 0; j < 2; ++j)
+        for (int k = 0; k < g.nmax; ++k)
+          if (ctx->lat.off[(static_cast<size_t>(d) * 2 + j) * g.nmax + k] > 0) hsh[d] |= static_cast<int8_t>(1 << j);
+    ok = ok && dalloc(&ctx->d_hsh, hsh.size()) == cudaSuccess &&
+         cudaMemcpy(ctx->d_hsh, hsh.data(), hsh.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    ctx->tma = ok;
+    if (!ok) cudaGetLastError();  // fall back to the plain-load sweep
   }
   if (trinity_reset(ctx) != TRINITY_OK) return bail(TRINITY_E_CUDA);
   *out = ctx;
@@ -1604,6 +1637,20 @@ int trinity_read_field(trinity_ctx* ctx, int what, int back, void* out, size_t b
   return TRINITY_OK;
 }
 
+int trinity_kernels_per_step(const trinity_ctx* ctx, int* n) {
+  if (!ctx || !n) return TRINITY_E_INVALID;
+  int k = 0;
+  if (ctx->two_level)
+    k = 1 + 1 + 1 + 1;  // sweep2, scatter, refine, tally
+  else if (ctx->tma && ctx->g.n_u >= 1.0f)
+    k = (ctx->ndir[0] > 0) + (ctx->ndir[1] > 0) + (ctx->ndir[2] > 0) + 1 + 1;  // sweeps, scatter, tally
+  else
+    k = 1 + 1 + 1;  // sweep, scatter, tally
+  if (ctx->n_iface > 0) k += ctx->two_level ? 2 : 1;  // interface split (and re-coarsening)
+  *n = k + 1;  // the step counter
+  return TRINITY_OK;
+}
+
 int trinity_steps_done(const trinity_ctx* ctx, int* n) {
   if (!ctx || !n) return TRINITY_E_INVALID;
   *n = ctx->steps_done;
@@ -1672,6 +1719,8 @@ void trinity_destroy(trinity_ctx* ctx) {
   cudaFree(ctx->d_xcls);
   cudaFree(ctx->d_b1tab);
   cudaFree(ctx->d_xmua);
+  for (int c = 0; c < 3; ++c) cudaFree(ctx->d_dlist[c]);
+  cudaFree(ctx->d_hsh);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   void* bufs[] = {ctx->I,         ctx->S,          ctx->Q,           ctx->mut,       ctx->eps,
                   ctx->nidx,      ctx->P32,        ctx->Pbf,         ctx->d_dirs,    ctx->d_offs,

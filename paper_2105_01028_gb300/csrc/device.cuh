@@ -141,6 +141,19 @@ cudaError_t launch_tally(const GridParams& g, const DirInfo* dirs, const float* 
                          const int* det_id, int n_det_entries, double* det, int nbins,
                          RunState rs, cudaStream_t st);
 cudaError_t launch_advance(const GridParams& g, RunState rs, cudaStream_t st);
+
+// The TMA-staged one-level sweep (sweep_tma.cu): uniform refractive index, vacuum faces,
+// nx a multiple of 4 and nx + 8 <= 256.  Tensor maps of the I and S rings, one per
+// dominant-axis class (box shapes differ), 128 bytes each as the driver encodes them.
+struct SweepMaps {
+  alignas(64) unsigned char I[3][128];
+  alignas(64) unsigned char S[3][128];
+};
+bool sweep_tma_supported(const GridParams& g);
+cudaError_t make_sweep_maps(const GridParams& g, float* Iring, float* Sring, SweepMaps* out);
+cudaError_t launch_sweep_tma(const GridParams& g, const DirInfo* dirs, const int* const dlist[3],
+                             const int ndir[3], const int8_t* offs, const int8_t* hsh, const SweepMaps& maps,
+                             const float* mut, float* Q, RunState rs, cudaStream_t st);
 cudaError_t launch_energy_density(const GridParams& g, const float* I, const float* nidx, float scale, float* u,
                                   cudaStream_t st);
 cudaError_t launch_interface(int nvox, int na, const int* vox, const int* rowptr, const int* src,

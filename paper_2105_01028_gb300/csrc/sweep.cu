@@ -141,8 +141,8 @@ __global__ void __launch_bounds__(256) sweep_kernel(GridParams g, const DirInfo*
         i1 = __ldg(i1p + u);
         s1v = __ldg(slev_s[m + 1] + u);
       }
-      Iup = (1.0f - f) * i0 + f * i1;
-      Sup = (1.0f - f) * s0v + f * s1v;
+      Iup = fmaf(f, i1, (1.0f - f) * i0);
+      Sup = fmaf(f, s1v, (1.0f - f) * s0v);
     } else if (g.mirror) {
       unsigned mask = 0u;
       const int cd = image_axis(qd, nd, 1u << dom, mask);
@@ -159,12 +159,12 @@ __global__ void __launch_bounds__(256) sweep_kernel(GridParams g, const DirInfo*
         i1 = __ldg(ilev_s[m + 1] + doff + img);
         s1v = __ldg(slev_s[m + 1] + doff + img);
       }
-      Iup = (1.0f - f) * i0 + f * i1;
-      Sup = (1.0f - f) * s0v + f * s1v;
+      Iup = fmaf(f, i1, (1.0f - f) * i0);
+      Sup = fmaf(f, s1v, (1.0f - f) * s0v);
     } else if (kind == 1 && v == g.src_voxel && src_amp != 0.0f) {
       const float on0 = (L0 >= 0 && L0 < g.pulse_steps) ? 1.0f : 0.0f;
       const float on1 = (L1 >= 0 && L1 < g.pulse_steps) ? 1.0f : 0.0f;
-      Iup = src_amp * ((1.0f - f) * on0 + f * on1);
+      Iup = src_amp * fmaf(f, on1, (1.0f - f) * on0);
     }
     float T, b0;
     if (kUniMu) {
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(GridParams g, const DirInfo*
       T = expf(-xo);
       b0 = ray_b0(xo, T);
     }
-    Q[lev0 + v] = Iup * T + Sup * b0;
+    Q[lev0 + v] = fmaf(Sup, b0, Iup * T);
   };
 
   for (int row = blockIdx.x * blockDim.y + threadIdx.y; row < nrows; row += gridDim.x * blockDim.y) {
