@@ -542,7 +542,6 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
       // Read the per-column tables through volatile views: they are loop-invariant, and if
       // the compiler hoists them out of the iteration loop they cost ~190 registers.
       const volatile float* vb1t = b1t;
-      const volatile uint8_t* vCls = sCls;
       float dmax = 0.0f, smax = 0.0f, cpart = 0.0f;
       // tcgen05.ld / st are warp-collective: a warp with any active row runs them on every
       // lane; inactive lanes keep S_old (so they rewrite the same X) and report no change.
@@ -658,50 +657,46 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
       } else {
         crow = 0.0f;
       }
-      // write out the voxels that stopped in this iteration: I = Q + b1 S, S (Q from
-      // registers: no global load on this path).  The addresses derive from a volatile
-      // shared copy of the plane size so the compiler cannot hoist 2 x HALF 64-bit
-      // addresses out of the iteration loop into registers.
-      if (__any_sync(0xffffffffu, mine)) {  // warp-uniform: the TMEM loads are collective
-        const size_t pl = static_cast<size_t>(*reinterpret_cast<volatile const int*>(&plane_s));
-        float* pI = Iring + cur_base + static_cast<size_t>(cb) * pl + v;
-        float* pS = Sring + cur_base + static_cast<size_t>(cb) * pl + v;
-        float esum_row = 0.0f;
-#pragma unroll
-        for (int ch = 0; ch < NCH; ++ch) {
-          const int c0 = cb + ch * CH;
-          float so[CH], qv_[CH];
-          tmem_ld<CH>(t_row + C::SOFF + c0, so);
-          if (ch < NCT) tmem_ld<CH>(t_q + ch * CH, qv_);
-          tmem_wait_ld();
-          if (ch >= NCT) {
-#pragma unroll
-            for (int j = 0; j < CH; ++j) qv_[j] = qr[(ch - NCT) * CH + j];
-          }
-#pragma unroll
-          for (int j = 0; j < CH; ++j) {
-            if (mine) {
-              const float b1 = kUniB1 ? reinterpret_cast<const volatile float*>(sB1c)[c0 + j]
-                                      : vb1t[vCls[c0 + j] * kM + row];
-              const float Iv = fmaf(b1, so[j], qv_[j]);
-              *pI = Iv;
-              *pS = so[j];
-              esum_row += Iv;
-              smax_loc = fmaxf(smax_loc, fabsf(so[j]));
-            }
-            pI += pl;
-            pS += pl;
-          }
-        }
-        if (mine) esum += static_cast<double>(esum_row) * static_cast<double>(nidx[v]);
-        // absorbed energy: mu_a sum_d I of the rows that stopped, one shared atomic per warp
-        float ab = mine ? esum_row * (ev * mut[v]) : 0.0f;
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) ab += __shfl_xor_sync(0xffffffffu, ab, o);
-        if (lane == 0) atomicAdd(&asum_sh, static_cast<double>(ab));
-      }
     }
     if (aborted) break;
+    // Write out the tile: I = Q + b1 S and S of every voxel, from TMEM (a voxel's S stays
+    // there unchanged once it has stopped).  At the tile's end, so that a warp stores whole
+    // 32-byte sectors (a brick row of eight voxels) instead of pieces as its rows stop.
+    {
+      const size_t pl = static_cast<size_t>(g.nv);
+      float* pI = Iring + cur_base + static_cast<size_t>(cb) * pl + v;
+      float* pS = Sring + cur_base + static_cast<size_t>(cb) * pl + v;
+      float esum_row = 0.0f;
+#pragma unroll
+      for (int ch = 0; ch < NCH; ++ch) {
+        const int c0 = cb + ch * CH;
+        float so[CH], qv_[CH];
+        tmem_ld<CH>(t_row + C::SOFF + c0, so);
+        if (ch < NCT) tmem_ld<CH>(t_q + ch * CH, qv_);
+        tmem_wait_ld();
+        if (ch >= NCT) {
+#pragma unroll
+          for (int j = 0; j < CH; ++j) qv_[j] = qr[(ch - NCT) * CH + j];
+        }
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+          if (vin) {
+            const float b1 = kUniB1 ? sB1c[c0 + j] : b1t[sCls[c0 + j] * kM + row];
+            const float Iv = fmaf(b1, so[j], qv_[j]);
+            pI[static_cast<size_t>(ch * CH + j) * pl] = Iv;
+            pS[static_cast<size_t>(ch * CH + j) * pl] = so[j];
+            esum_row += Iv;
+            smax_loc = fmaxf(smax_loc, fabsf(so[j]));
+          }
+        }
+      }
+      if (vin) esum += static_cast<double>(esum_row) * static_cast<double>(nidx[v]);
+      // absorbed energy: mu_a sum_d I, one shared atomic per warp
+      float ab = vin ? esum_row * (ev * mut[v]) : 0.0f;
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) ab += __shfl_xor_sync(0xffffffffu, ab, o);
+      if (lane == 0) atomicAdd(&asum_sh, static_cast<double>(ab));
+    }
     // iteration statistics of this tile (group-0 threads hold one row each)
     if (warp < 4) {
       int im = vin ? iters : 0;
