@@ -254,8 +254,11 @@ def workload_config(args, precision=None):
                 args.spinup + args.warmup, args.spinup + args.warmup + args.steps - 1),
             "tol": 1e-6, "l2": "inputs larger than L2 (%s time-level history per solve)" % hist,
             "parallelism": "replicas" if dist_env()[0] > 1 else "single GPU",
-            "precision": precision or ("fp32" if args.exact else args.precision),
-            "source_function": "exact per-voxel solve S = M Q" if args.exact else "source iteration (Eq. 12)"}
+            "precision": precision or (("fp32" if args.exact_simt else "3xtf32") if args.exact else args.precision),
+            "source_function": (("exact per-voxel solve S = M Q, " +
+                                 ("FP32 SIMT products" if args.exact_simt else
+                                  "three TF32 tensor-core products with FP32 accumulation"))
+                                if args.exact else "source iteration (Eq. 12)")}
 
 
 def run_serve(args):
@@ -605,6 +608,8 @@ def main():
     ap.add_argument("--slots", type=int, default=8, help="served stream concurrent slots")
     ap.add_argument("--exact", action="store_true",
                     help="exact per-voxel source function (one optics class on the slab) instead of the iteration")
+    ap.add_argument("--exact-simt", action="store_true",
+                    help="with --exact: the FP32 SIMT form instead of the tensor cores")
     ap.add_argument("--two-level", action="store_true",
                     help="slab on the paper's fiducial angles: 3072 transport, 192 source-function dirs")
     ap.add_argument("--adjoint", action="store_true", help="gradient workload (checkpointed adjoint)")
@@ -638,7 +643,7 @@ def main():
     else:
         prob = W.config_slab(steps=total, precision=args.precision, nx=nx, ny=ny, nz=nz)
     if args.exact:
-        prob["exact"] = True
+        prob["exact"] = "simt" if args.exact_simt else True
     stream = torch.cuda.Stream()
     nv = prob["nx"] * prob["ny"] * prob["nz"]
     na = 12 * prob["nside"] ** 2          # transport directions (updates are counted on these)
@@ -684,6 +689,8 @@ def main():
     k_mean = float(np.mean(k_it_mean[-kp:]))
     executed = fwd.executed_iterations()[first:first + args.steps]
     kps = fwd.kernels_per_step()
+    xform = fwd.exact_form()
+    sweep_kernel = {"plain": "sweep_kernel", "tma": "sweep_tma_kernel", "two-level": "sweep2_kernel"}[fwd.sweep_form()]
     fwd.close()
 
     updates = nv * na * args.steps
@@ -707,16 +714,29 @@ def main():
     else:
         s_bound, s_peak, s_unit = "alu", fp32_peak, "TFLOP/s"
     s_ach = scat_flops / (per[1] * 1e-3) / 1e12
+    s_name = "exact_fp32" if args.exact else "scatter_" + args.precision
+    tc_extra = {}
+    if args.exact and xform == "tc":
+        # one product per voxel: HBM-bound (Q in, I and S out: 12 B per update, plus the
+        # voxel's class, index and optics bytes); the tensor pipe runs three TF32 products
+        s_name, s_bound, s_peak, s_unit = "exact_tc", "hbm", hbm, "GB/s"
+        x_bytes = nv * na_s * 12 + nv * 5
+        s_ach = x_bytes / (per[1] * 1e-3) / 1e9
+        tf32_peak = pk.get("bf16_tflops", 1900.0) * 1.1 / 2.25  # measured BF16 x nominal TF32/BF16
+        tc_tf = 3 * scat_flops / (per[1] * 1e-3) / 1e12
+        tc_extra = {"algorithmic_bytes": x_bytes, "tensor_tflops_3xtf32": tc_tf,
+                    "tensor_frac_of_tf32": tc_tf / tf32_peak,
+                    "tf32_peak": "%.0f TFLOP/s (measured BF16 burst x 1.1/2.25 nominal ratio)" % tf32_peak}
     w_ach = sweep_bytes / (per[0] * 1e-3) / 1e9
     kernels = [
         {"name": "sweep", "ms": per[0], "share": per[0] / tot, "bound": "hbm",
          "achieved": w_ach, "peak": hbm, "unit": "GB/s", "frac": w_ach / hbm,
          "algorithmic_bytes": sweep_bytes,
-         "traffic": measured_traffic("sweep2_kernel" if nch > 1 else "sweep_kernel", nv * na)},
-        {"name": "exact_fp32" if args.exact else "scatter_" + args.precision, "ms": per[1], "share": per[1] / tot,
-         "bound": s_bound, "achieved": s_ach, "peak": s_peak, "unit": s_unit,
-         "frac": s_ach / s_peak, "algorithmic_flops": scat_flops,
-         "hbm_gbs": scat_bytes / (per[1] * 1e-3) / 1e9},
+         "traffic": measured_traffic(sweep_kernel, nv * na)},
+        dict({"name": s_name, "ms": per[1], "share": per[1] / tot,
+              "bound": s_bound, "achieved": s_ach, "peak": s_peak, "unit": s_unit,
+              "frac": s_ach / s_peak, "algorithmic_flops": scat_flops,
+              "hbm_gbs": scat_bytes / (per[1] * 1e-3) / 1e9}, **tc_extra),
         {"name": "tally+advance", "ms": per[2], "share": per[2] / tot},
     ]
     if nch > 1:
@@ -726,10 +746,10 @@ def main():
                       "achieved": f_ach, "peak": hbm, "unit": "GB/s", "frac": f_ach / hbm,
                       "algorithmic_bytes": fin_bytes}
     dom = max(kernels[:2], key=lambda k: k["ms"])
-    scat_kernel = ("exact_gemm192_kernel" if args.exact else
+    scat_kernel = (("exact_tc_kernel" if xform == "tc" else "exact_gemm192_kernel") if args.exact else
                    "scatter_tc_kernel" if args.precision == "bf16" else "scatter_fp32_kernel")
     traffic = (measured_traffic(scat_kernel, nv * na_s) if dom is kernels[1]
-               else measured_traffic("sweep2_kernel" if nch > 1 else "sweep_kernel", nv * na))
+               else measured_traffic(sweep_kernel, nv * na))
     roof = {"kernel": dom["name"], "bound": dom["bound"], "achieved": dom["achieved"],
             "peak": dom["peak"], "unit": dom["unit"], "frac": dom["frac"], "traffic": traffic,
             "peak_source": pk["_source"] + (" (FP32 FFMA: %d SMs x 128 lanes x 2 x max SM clock)" % sm_count()
@@ -738,7 +758,8 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if (args.exact or args.precision == "fp32") else "bf16-scatter/f32-sweep",
+            "dtype": (("3xtf32-product/f32-sweep" if xform == "tc" else "f32") if args.exact else
+                      "f32" if args.precision == "fp32" else "bf16-scatter/f32-sweep"),
             "data": "synthetic", "config": workload_config(args),
             "gpu_launches": kps * args.steps,
             "iterations": {"mean": float(np.mean(win_mean)), "max": int(np.max(win_max)),

@@ -135,13 +135,26 @@ int trinity_set_fresnel(trinity_ctx* ctx, int on);
  * M = (I - a P B1)^-1 a P (B1 = diag b1(mu_t ds_d)), so with ``on`` set each step takes
  * S = M Q in one product per voxel.  The operators are built on the host in FP64 (from
  * the FP32 phase matrix with its diagonal correction, the matrix the iteration applies)
- * at this call and at every trinity_set_optics, and applied in FP32 in either precision
- * mode.  TRINITY_E_UNSUPPORTED if the optics have more than 8 distinct pairs (the mode
- * is then off) or on a two-level angular grid.  Before the first step. */
+ * at this call and at every trinity_set_optics, and applied in either precision mode in
+ * one of two forms:
+ *   on = 1: on the tensor cores where the grid allows it (192 directions and a voxel count
+ *           that is a multiple of 4): three TF32 products, M_hi Q_hi + M_hi Q_lo +
+ *           M_lo Q_hi with x_hi = tf32(x), x_lo = tf32(x - x_hi), accumulated in FP32
+ *           (each operand carries ~22 significant bits; M and Q are non-negative, so the
+ *           result is within a few 2^-22 of the FP32 product); otherwise as on = 2;
+ *   on = 2: FP32 products on the SIMT cores;
+ *   on = 0: off (the source iteration).
+ * TRINITY_E_UNSUPPORTED if the optics have more than 8 distinct pairs (the mode is then
+ * off) or on a two-level angular grid; TRINITY_E_INVALID for another ``on``.  Before the
+ * first step. */
 int trinity_set_exact_solve(trinity_ctx* ctx, int on);
 
 /* Number of optics classes the exact solve uses (0 when it is off). */
 int trinity_exact_classes(const trinity_ctx* ctx, int* n);
+
+/* Form of the exact solve that runs: 1 tensor cores, 2 FP32 SIMT, 0 off (or no optics
+ * set yet). */
+int trinity_exact_form(const trinity_ctx* ctx, int* form);
 
 /* Number of interface voxels in the context's current table. */
 int trinity_interface_count(const trinity_ctx* ctx, int* n);
@@ -233,6 +246,11 @@ int trinity_steps_done(const trinity_ctx* ctx, int* n);
 /* Kernel launches one time step issues with the context's current inputs (sweep or
  * sweeps, interface split, source iteration, tallies, step counter). */
 int trinity_kernels_per_step(const trinity_ctx* ctx, int* n);
+
+/* Form of the ray sweep a step runs: 0 plain loads (one kernel), 1 upwind planes staged
+ * through TMA tile loads (one kernel per dominant-axis class: vacuum faces, a uniform
+ * refractive index, nx a multiple of 4), 2 the fused two-level sweep. */
+int trinity_sweep_form(const trinity_ctx* ctx, int* form);
 
 /* Zero the fields, tallies and step counter; keep grid, optics, source and detectors. */
 int trinity_reset(trinity_ctx* ctx);

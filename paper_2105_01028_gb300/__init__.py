@@ -82,8 +82,9 @@ class Forward:
         self._check(self.set_optics(prob["mua"], prob["mus"], prob["nidx"], prob["g"]))
         if prob.get("fresnel", False):
             self._check(self.L.trinity_set_fresnel(self.h, 1))
-        if prob.get("exact", False):
-            self._check(self.L.trinity_set_exact_solve(self.h, 1))
+        ex = prob.get("exact", False)
+        if ex:  # True / "tc": tensor cores where the grid allows; "simt": FP32 SIMT form
+            self._check(self.L.trinity_set_exact_solve(self.h, 2 if ex == "simt" else 1))
         src = prob.get("source")
         if src is not None:
             self._check(self.L.trinity_set_source(self.h, int(src["face"]), float(src["u_mm"]),
@@ -130,6 +131,12 @@ class Forward:
         n = ctypes.c_int()
         self._check(self.L.trinity_exact_classes(self.h, ctypes.byref(n)))
         return n.value
+
+    def exact_form(self):
+        """Form of the exact solve that runs: "tc" (tensor cores), "simt" (FP32 SIMT) or None."""
+        f = ctypes.c_int()
+        self._check(self.L.trinity_exact_form(self.h, ctypes.byref(f)))
+        return {0: None, 1: "tc", 2: "simt"}[f.value]
 
     def interface_count(self):
         n = ctypes.c_int()
@@ -224,6 +231,12 @@ class Forward:
         n = ctypes.c_int()
         self._check(self.L.trinity_kernels_per_step(self.h, ctypes.byref(n)))
         return n.value
+
+    def sweep_form(self):
+        """Form of the ray sweep: "plain", "tma" (TMA-staged upwind planes) or "two-level"."""
+        f = ctypes.c_int()
+        self._check(self.L.trinity_sweep_form(self.h, ctypes.byref(f)))
+        return ("plain", "tma", "two-level")[f.value]
 
     def steps_done(self):
         n = ctypes.c_int()

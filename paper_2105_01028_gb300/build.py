@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libtrinity.so")
 SOURCES = ["host_tables.cpp", "kernels.cu", "sweep.cu", "sweep_tma.cu", "scatter_tc.cu", "api.cu", "serve.cpp",
-           "noalloc.cu", "adjoint.cu", "twolevel.cu", "exact.cu"]
+           "noalloc.cu", "adjoint.cu", "twolevel.cu", "exact.cu", "exact_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -102,7 +102,12 @@ struct trinity_ctx {
 
   // exact per-voxel source function for piecewise-uniform optics
   bool exact = false;
+  int exact_mode = 0;          // 1: tensor-core form where it applies, 2: FP32 SIMT form
+  bool exact_tc = false;       // the tensor-core form runs
   int n_xcls = 0;
+  float* d_Mimg = nullptr;     // [classes][6 chunks][hi, lo][192][32] operator images (tensor-core form)
+  uint8_t* d_tmask = nullptr;  // [128-voxel tiles] classes present in each tile
+  alignas(64) unsigned char qmap[128] = {};  // TMA descriptor of Q (tensor-core form)
   float* d_Mt = nullptr;       // [classes][na][na] operators M = (I - a P B1)^-1 a P, transposed
   float* d_b1tab = nullptr;    // [classes][na] b1 of each class and direction
   float* d_xmua = nullptr;     // [classes] mu_a of each class (absorbed-energy tally)
@@ -544,7 +549,10 @@ int enqueue_transport(trinity_ctx* ctx, const RunState& rs) {
 // The per-voxel source iteration (Eq. 12) on the source function's directions.
 int enqueue_scatter(trinity_ctx* ctx, const RunState& rs) {
   const GridParams& gs = ctx->g_s;
-  if (ctx->exact) {
+  if (ctx->exact && ctx->exact_tc) {
+    CK(launch_exact_tc(gs, ctx->qmap, ctx->d_Mimg, ctx->d_tmask, ctx->d_b1tab, ctx->n_xcls, ctx->d_xcls,
+                       ctx->d_xmua, ctx->Qc, ctx->nidx, ctx->Ic, ctx->S, rs, ctx->stream));
+  } else if (ctx->exact) {
     CK(launch_exact_fp32(gs, ctx->d_b1ds, ctx->nch, ctx->d_Mt, ctx->d_b1tab, ctx->d_xcls, ctx->d_xmua, ctx->Qc,
                          ctx->mut, ctx->nidx, ctx->Ic, ctx->S, rs, ctx->stream));
   } else if (ctx->desc.precision == TRINITY_BF16) {
@@ -632,6 +640,7 @@ int build_exact(trinity_ctx* ctx) {
       Pt[static_cast<size_t>(i) * na + j] =
           static_cast<double>(ctx->h_P32[static_cast<size_t>(i) * na + j]) + (i == j ? double(ctx->h_rc32[i]) : 0.0);
   std::vector<float> Mt(pairs.size() * static_cast<size_t>(na) * na);
+  std::vector<double> Mall(pairs.size() * static_cast<size_t>(na) * na);
   std::vector<float> b1tab(pairs.size() * static_cast<size_t>(na));
   for (size_t c = 0; c < pairs.size(); ++c) {
     const double mt = pairs[c].first, a = 1.0 - static_cast<double>(pairs[c].second);
@@ -654,8 +663,10 @@ int build_exact(trinity_ctx* ctx) {
       return fail(ctx, TRINITY_E_INVALID, e.what());
     }
     for (int i = 0; i < na; ++i)
-      for (int j = 0; j < na; ++j)
+      for (int j = 0; j < na; ++j) {
         Mt[(c * na + j) * static_cast<size_t>(na) + i] = static_cast<float>(M[static_cast<size_t>(i) * na + j]);
+        Mall[(c * na + i) * static_cast<size_t>(na) + j] = M[static_cast<size_t>(i) * na + j];
+      }
   }
   // mu_a of each class, formed as the iteration kernels form it (eps * mu_t in FP32)
   std::vector<float> xmua(pairs.size());
@@ -677,6 +688,24 @@ int build_exact(trinity_ctx* ctx) {
   CK(cudaMemcpy(ctx->d_b1tab, b1tab.data(), b1tab.size() * 4, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_xcls, cls.data(), nv, cudaMemcpyHostToDevice));
   ctx->n_xcls = static_cast<int>(pairs.size());
+  // the tensor-core form: operator images, per-tile class masks and Q's TMA descriptor
+  cudaFree(ctx->d_Mimg);
+  cudaFree(ctx->d_tmask);
+  ctx->d_Mimg = nullptr;
+  ctx->d_tmask = nullptr;
+  ctx->exact_tc = false;
+  if (ctx->exact_mode != 2 && exact_tc_supported(ctx->g_s, ctx->n_xcls) &&
+      make_exact_qmap(ctx->g_s, ctx->Qc, ctx->qmap) == cudaSuccess) {
+    std::vector<float> img;
+    std::vector<uint8_t> mask;
+    exact_tc_images(Mall.data(), ctx->n_xcls, &img);
+    exact_tc_tile_masks(cls.data(), static_cast<int>(nv), &mask);
+    CK(dalloc(&ctx->d_Mimg, img.size()));
+    CK(dalloc(&ctx->d_tmask, mask.size()));
+    CK(cudaMemcpy(ctx->d_Mimg, img.data(), img.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_tmask, mask.data(), mask.size(), cudaMemcpyHostToDevice));
+    ctx->exact_tc = true;
+  }
   return TRINITY_OK;
 }
 
@@ -1024,15 +1053,26 @@ int trinity_set_fresnel(trinity_ctx* ctx, int on) {
 int trinity_set_exact_solve(trinity_ctx* ctx, int on) {
   if (!ctx) return TRINITY_E_INVALID;
   if (ctx->locked) return fail(ctx, TRINITY_E_STATE, "the exact solve must be chosen before the first step");
+  if (on < 0 || on > 2) return fail(ctx, TRINITY_E_INVALID, "exact solve: on must be 0, 1 or 2");
   ctx->exact = on != 0;
+  ctx->exact_mode = on;
   const int rc = build_exact(ctx);
-  if (rc != TRINITY_OK) ctx->exact = false;
+  if (rc != TRINITY_OK) {
+    ctx->exact = false;
+    ctx->exact_tc = false;
+  }
   return rc;
 }
 
 int trinity_exact_classes(const trinity_ctx* ctx, int* n) {
   if (!ctx || !n) return TRINITY_E_INVALID;
   *n = ctx->exact ? ctx->n_xcls : 0;
+  return TRINITY_OK;
+}
+
+int trinity_exact_form(const trinity_ctx* ctx, int* form) {
+  if (!ctx || !form) return TRINITY_E_INVALID;
+  *form = !ctx->exact || !ctx->optics_set ? 0 : (ctx->exact_tc ? 1 : 2);
   return TRINITY_OK;
 }
 
@@ -1651,6 +1691,12 @@ int trinity_kernels_per_step(const trinity_ctx* ctx, int* n) {
   return TRINITY_OK;
 }
 
+int trinity_sweep_form(const trinity_ctx* ctx, int* form) {
+  if (!ctx || !form) return TRINITY_E_INVALID;
+  *form = ctx->two_level ? 2 : ((ctx->tma && ctx->g.n_u >= 1.0f) ? 1 : 0);
+  return TRINITY_OK;
+}
+
 int trinity_steps_done(const trinity_ctx* ctx, int* n) {
   if (!ctx || !n) return TRINITY_E_INVALID;
   *n = ctx->steps_done;
@@ -1719,6 +1765,8 @@ void trinity_destroy(trinity_ctx* ctx) {
   cudaFree(ctx->d_xcls);
   cudaFree(ctx->d_b1tab);
   cudaFree(ctx->d_xmua);
+  cudaFree(ctx->d_Mimg);
+  cudaFree(ctx->d_tmask);
   for (int c = 0; c < 3; ++c) cudaFree(ctx->d_dlist[c]);
   cudaFree(ctx->d_hsh);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);

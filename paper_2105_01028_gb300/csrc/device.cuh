@@ -3,6 +3,7 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <vector>
 
 namespace trinity {
 
@@ -215,5 +216,21 @@ cudaError_t launch_exact_fp32(const GridParams& g, const float* b1ds, int nch, c
                               const float* b1tab, const uint8_t* cls, const float* mua_cls, const float* Q,
                               const float* mut, const float* nidx, float* Iring, float* Sring, RunState rs,
                               cudaStream_t st);
+
+// The exact solve on the tensor cores (defined in exact_tc.cu): three TF32 products with
+// FP32 accumulation in TMEM, for 192 directions, a voxel count that is a multiple of 4
+// (the TMA's 16-byte row rule on Q) and at most 8 optics classes.
+bool exact_tc_supported(const GridParams& g, int ncls);
+int exact_tc_tiles(int nv);
+// M: [classes][192][192] FP64 (row i = output direction); img receives the operators'
+// shared-memory images (per class and 32-direction chunk: TF32 hi, then lo).
+void exact_tc_images(const double* M, int ncls, std::vector<float>* img);
+// Bit c of mask[t] is set when 128-voxel tile t holds a voxel of class c.
+void exact_tc_tile_masks(const uint8_t* cls, int nv, std::vector<uint8_t>* mask);
+// The TMA descriptor of Q ([192][nv] FP32) for 128-voxel x 32-direction boxes; out is 128 bytes.
+cudaError_t make_exact_qmap(const GridParams& g, const float* Q, void* out);
+cudaError_t launch_exact_tc(const GridParams& g, const void* qmap, const float* Mimg, const uint8_t* tmask,
+                            const float* b1tab, int ncls, const uint8_t* cls, const float* mua_cls, const float* Q,
+                            const float* nidx, float* Iring, float* Sring, RunState rs, cudaStream_t st);
 
 }  // namespace trinity

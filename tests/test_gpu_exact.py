@@ -4,7 +4,9 @@ iteration on the CPU (test_oracle_exact.py).
 
 Bars are the FP32 bar of the iteration (test_gpu_parity.py): 1e-5 of the peak for
 detector curves, energy and whole fields.  The exact path replaces the iteration's
-stopping error by one FP32 product with an operator that the host builds in FP64.
+stopping error by one product with an operator that the host builds in FP64: on the
+tensor cores at 192 directions (three TF32 products, ~22 significant bits per operand,
+FP32 accumulation), else FP32 on the SIMT cores; both are held to the same bar.
 """
 import numpy as np
 import pytest
@@ -29,7 +31,7 @@ def _run(p, steps):
     fw = P.Forward(p)
     fw.step(steps)
     out = dict(det=fw.detectors(), N=fw.energy()[0], I=fw.field(P.FIELD_I), S=fw.field(P.FIELD_S),
-               classes=fw.exact_classes())
+               classes=fw.exact_classes(), form=fw.exact_form(), absorbed=fw.balance()["absorbed"])
     fw.close()
     return out
 
@@ -43,6 +45,7 @@ def test_exact_matches_oracle(nside):
     ref = s.run(steps)
     g = _run(p, steps)
     assert g["classes"] == 3
+    assert g["form"] == ("tc" if nside == 4 else "simt")  # 800 voxels: six tiles and a ragged one
     assert np.max(np.abs(g["det"] - ref["detectors"])) <= DET_TOL * np.max(np.abs(ref["detectors"]))
     assert np.max(np.abs(g["N"] - ref["energy"])) <= DET_TOL * np.max(ref["energy"])
     I_ref, S_ref = s.level("I"), s.level("S")
@@ -57,6 +60,50 @@ def test_exact_agrees_with_the_converged_gpu_iteration():
     assert it["classes"] == 0 and ex["classes"] == 3
     assert np.max(np.abs(it["det"] - ex["det"])) <= DET_TOL * np.max(np.abs(ex["det"]))
     assert np.max(np.abs(it["I"] - ex["I"])) <= FIELD_TOL * np.max(np.abs(ex["I"]))
+
+
+def test_tensor_core_and_simt_forms_agree():
+    """The two forms of the exact solve on the phantom (three classes, tiles that mix
+    them, a ragged last tile), after enough steps for light to cross the interfaces."""
+    p = phantom(nside=4, steps=10, tol=1e-6)
+    tc = _run(dict(p, exact=True), 10)
+    simt = _run(dict(p, exact="simt"), 10)
+    assert tc["form"] == "tc" and simt["form"] == "simt"
+    for k in ("det", "N", "I", "S", "absorbed"):
+        assert np.max(np.abs(tc[k] - simt[k])) <= FIELD_TOL * np.max(np.abs(simt[k])), k
+
+
+def test_tensor_core_form_with_eight_classes():
+    """Eight optics classes (the most the exact solve takes) in stripes along x, so every
+    128-voxel tile holds several of them: against the oracle."""
+    steps = 8
+    p = W.homogeneous(16, 8, 6, 4, 0.02, 2.0, g=0.9, steps=steps, tol=1e-6)
+    p["max_iters"] = 20000
+    mua, mus = np.array(p["mua"], np.float32), np.array(p["mus"], np.float32)
+    x = np.arange(16)
+    for c in range(8):
+        sel = (x // 2) == c
+        mua[:, :, sel] = np.float32(0.01 + 0.01 * c)
+        mus[:, :, sel] = np.float32(1.0 + 0.25 * c)
+    p["mua"], p["mus"] = mua, mus
+    p["source"] = dict(face=4, u_mm=8.0, v_mm=4.0, half_angle_deg=20.0, pulse_steps=2, energy=1.0)
+    p["detectors"] = [dict(face=4, u_mm=10.5, v_mm=4.5, radius_mm=1.0, half_angle_deg=20.0)]
+    p = W._bins(p)
+    g = _run(dict(p, exact=True), steps)
+    assert g["classes"] == 8 and g["form"] == "tc"
+    s = ExactSolver(dict(p, mua=np.asarray(p["mua"], np.float64), mus=np.asarray(p["mus"], np.float64)))
+    ref = s.run(steps)
+    assert np.max(np.abs(g["det"] - ref["detectors"])) <= DET_TOL * np.max(np.abs(ref["detectors"]))
+    I_ref, S_ref = s.level("I"), s.level("S")
+    assert np.max(np.abs(g["I"] - I_ref)) <= FIELD_TOL * np.max(np.abs(I_ref))
+    assert np.max(np.abs(g["S"] - S_ref)) <= FIELD_TOL * np.max(np.abs(S_ref))
+
+
+def test_voxel_count_not_a_multiple_of_four_takes_the_simt_form():
+    p = W.config_slab(steps=4, nx=9, ny=9, nz=7)
+    p["exact"] = True
+    g = _run(p, 4)
+    assert g["classes"] == 1 and g["form"] == "simt"
 
 
 def test_bf16_context_takes_the_same_exact_path():
