@@ -12,16 +12,19 @@
 //   dom z: an item is R rows along y of one z slab; the upwind rows are those of slab
 //          z - sgn shifted by the slab's lattice offsets (one contiguous (x, y) box);
 //   dom y: R rows along z of one y slab, likewise;
-//   dom x: a 4 x 4 block of (y, z) rows; the upwind sample of voxel x lies in slab x - sgn
-//          shifted by that slab's offsets, so the box covers the block plus one row of
-//          halo (5 x 5 rows) and each voxel picks its row in shared memory.  A direction's
-//          offsets along a transverse axis all have the sign of its slope there (they are
-//          differences of a monotone floor), so the halo lies on one side only:
-//          hsh[d] bit 0 / 1 is set when the y / z offsets are positive (the upwind rows are
-//          then y - 1 .. y + 3, else y .. y + 4).
-// Boxes start at x = -4 (the TMA's 16-byte rule on the innermost coordinate) and span
-// nx + 8 floats; coordinates outside the box read zero, which is the vacuum boundary's
-// "nothing enters through a side face".  The source face's inflow is added per voxel.
+//   dom x: a 4 x 4 block of (y, z) rows over a chunk of 32 voxels along x; the upwind
+//          sample of voxel x lies in slab x - sgn shifted by that slab's offsets, so the
+//          box covers the block plus one row of halo (5 x 5 rows) and each voxel picks its
+//          row in shared memory.  A direction's offsets along a transverse axis all have
+//          the sign of its slope there (they are differences of a monotone floor), so the
+//          halo lies on one side only: hsh[d] bit 0 / 1 is set when the y / z offsets are
+//          positive (the upwind rows are then y - 1 .. y + 3, else y .. y + 4).  Along x
+//          the box spans the chunk plus four floats on the upwind side (x0 - 4 .. x0 + 31
+//          for sgn > 0, x0 .. x0 + 35 for sgn < 0: the TMA's 16-byte rule on the innermost
+//          coordinate), so its size does not grow with nx.
+// dom y / z boxes span the rows' nx floats from x = 0; coordinates outside a box read
+// zero, which is the vacuum boundary's "nothing enters through a side face".  The source
+// face's inflow is added per voxel.
 // The tensor maps view a whole ring (5 levels x N_a planes) as one 4-D tensor
 // (x, y, z, plane), built on the host by the driver's encoder.
 #include <cuda.h>
@@ -39,6 +42,8 @@ namespace {
 
 constexpr int kRows = 16;       // rows per item (dom y, z)
 constexpr int kBlk = 4;         // rows per item along each transverse axis (dom x)
+constexpr int kXc = 32;         // voxels per item along x (dom x)
+constexpr int kXw = kXc + 4;    // box width along x (dom x): the chunk and a 4-float upwind halo
 constexpr int kPad = 0;         // box rows cover x in [0, nx) exactly (no out-of-range x)
 constexpr int kStages = 2;      // items in flight per CTA
 constexpr long long kTmaWait = 2000000000LL;  // ~1 s bound on every mbarrier wait
@@ -103,6 +108,7 @@ struct ItemInfo {
   DirStep s;
   int oy, oz;   // box origin (y, z)
   int ra, rb;   // dom z: (z, y0); dom y: (y, z0); dom x: (y0, z0)
+  int x0, ox;   // first voxel along x of the item; box origin along x
   int kp;       // slab index of the item's voxels (dom y, z)
   int dx;       // x shift of the upwind samples (dom y, z)
 };
@@ -117,7 +123,7 @@ __global__ void __launch_bounds__(256) sweep_tma_kernel(GridParams g, const DirI
                                                         const float* __restrict__ mut, float* __restrict__ Q,
                                                         RunState rs, int first) {
   using B = Box<DOM>;
-  const int W = g.nx + 2 * kPad;
+  const int W = DOM == 0 ? kXw : g.nx + 2 * kPad;
   // floats per box slot: a TMA tile's shared-memory destination must be 128-byte aligned,
   // so each slot is rounded up to 32 floats
   const int box = (W * B::RY * B::RZ + 31) & ~31;
@@ -138,7 +144,8 @@ __global__ void __launch_bounds__(256) sweep_tma_kernel(GridParams g, const DirI
   // items of one direction
   const int ipd = DOM == 2 ? g.nz * ((g.ny + kRows - 1) / kRows)
                            : (DOM == 1 ? g.ny * ((g.nz + kRows - 1) / kRows)
-                                       : ((g.ny + kBlk - 1) / kBlk) * ((g.nz + kBlk - 1) / kBlk));
+                                       : ((g.ny + kBlk - 1) / kBlk) * ((g.nz + kBlk - 1) / kBlk) *
+                                             ((g.nx + kXc - 1) / kXc));
   const int nitems = ndir * ipd;
   if (tid == 0) {
     for (int k = 0; k < kStages; ++k) bar_init(&bar[k]);
@@ -184,6 +191,8 @@ __global__ void __launch_bounds__(256) sweep_tma_kernel(GridParams g, const DirI
       it.oy = y0 - (it.kp > 0 ? off1[it.kp] : 0);
       it.oz = z - s.sgn;
       it.dx = it.kp > 0 ? off0[it.kp] : 0;
+      it.x0 = 0;
+      it.ox = -kPad;
     } else if (DOM == 1) {
       const int nzb = (g.nz + kRows - 1) / kRows;
       const int y = t / nzb, z0 = (t % nzb) * kRows;
@@ -193,9 +202,14 @@ __global__ void __launch_bounds__(256) sweep_tma_kernel(GridParams g, const DirI
       it.oy = y - s.sgn;
       it.oz = z0 - (it.kp > 0 ? off1[it.kp] : 0);
       it.dx = it.kp > 0 ? off0[it.kp] : 0;
+      it.x0 = 0;
+      it.ox = -kPad;
     } else {
-      const int nyb = (g.ny + kBlk - 1) / kBlk;
-      const int zb = t / nyb, yb = t % nyb;
+      const int nyb = (g.ny + kBlk - 1) / kBlk, nxc = (g.nx + kXc - 1) / kXc;
+      const int xc = t % nxc, t2 = t / nxc;
+      const int zb = t2 / nyb, yb = t2 % nyb;
+      it.x0 = xc * kXc;
+      it.ox = s.sgn > 0 ? it.x0 - 4 : it.x0;
       it.ra = yb * kBlk;
       it.rb = zb * kBlk;
       const int h = hsh[s.d];
@@ -214,12 +228,12 @@ __global__ void __launch_bounds__(256) sweep_tma_kernel(GridParams g, const DirI
     const uint32_t bytes = static_cast<uint32_t>(W * B::RY * B::RZ) * 4u * ((s.h0 ? 2u : 0u) + (s.h1 ? 2u : 0u));
     bar_expect(&bar[stage], bytes);
     if (s.h0) {
-      tma_load4(base + 0 * box, &tmI, -kPad, it.oy, it.oz, s.p0, &bar[stage]);
-      tma_load4(base + 2 * box, &tmS, -kPad, it.oy, it.oz, s.p0, &bar[stage]);
+      tma_load4(base + 0 * box, &tmI, it.ox, it.oy, it.oz, s.p0, &bar[stage]);
+      tma_load4(base + 2 * box, &tmS, it.ox, it.oy, it.oz, s.p0, &bar[stage]);
     }
     if (s.h1) {
-      tma_load4(base + 1 * box, &tmI, -kPad, it.oy, it.oz, s.p1, &bar[stage]);
-      tma_load4(base + 3 * box, &tmS, -kPad, it.oy, it.oz, s.p1, &bar[stage]);
+      tma_load4(base + 1 * box, &tmI, it.ox, it.oy, it.oz, s.p1, &bar[stage]);
+      tma_load4(base + 3 * box, &tmS, it.ox, it.oy, it.oz, s.p1, &bar[stage]);
     }
   };
 
@@ -290,18 +304,22 @@ __global__ void __launch_bounds__(256) sweep_tma_kernel(GridParams g, const DirI
         }
       }
     } else {
-      // warps over the block's 16 rows, lanes along x; each x has its own slab offsets
+      // warps over the block's 16 rows, lanes along the item's voxels in x; each x has its
+      // own slab offsets
       const int8_t* off0 = offs + (static_cast<size_t>(s.d) * 2 + 0) * g.nmax;
       const int8_t* off1 = offs + (static_cast<size_t>(s.d) * 2 + 1) * g.nmax;
-      for (int r = warp; r < kBlk * kBlk; r += 8) {
-        const int y = it.ra + (r % kBlk), z = it.rb + (r / kBlk);
-        if (y >= g.ny || z >= g.nz) continue;
-        const int vrow = (z * g.ny + y) * g.nx;
-        for (int x = lane; x < g.nx; x += 32) {
-          const int kp = s.sgn > 0 ? x : g.nx - 1 - x;
-          const int dy = kp > 0 ? off0[kp] : 0, dz = kp > 0 ? off1[kp] : 0;
-          const int xs = x - s.sgn;
-          emit(vrow + x, ((z - it.oz - dz) * B::RY + (y - it.oy - dy)) * W + xs, xs, kp == 0);
+#pragma unroll
+      for (int xl = lane; xl < kXc; xl += 32) {
+        const int x = it.x0 + xl;
+        if (x >= g.nx) break;
+        const int kp = s.sgn > 0 ? x : g.nx - 1 - x;
+        const int dy = kp > 0 ? off0[kp] : 0, dz = kp > 0 ? off1[kp] : 0;
+        const int xs = x - s.sgn;
+        for (int r = warp; r < kBlk * kBlk; r += 8) {
+          const int y = it.ra + (r % kBlk), z = it.rb + (r / kBlk);
+          if (y >= g.ny || z >= g.nz) continue;
+          emit((z * g.ny + y) * g.nx + x, ((z - it.oz - dz) * B::RY + (y - it.oy - dy)) * W + (xs - it.ox), xs,
+               kp == 0);
         }
       }
     }
@@ -323,8 +341,8 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 bool sweep_tma_supported(const GridParams& g) {
   if (g.periodic || g.mirror || g.nx % 4 != 0 || g.nx + 2 * kPad > 256) return false;
-  // the largest item (dom x: the block plus its halo) must fit the shared memory of a CTA
-  const size_t slot = (static_cast<size_t>(g.nx + 2 * kPad) * (kBlk + 1) * (kBlk + 1) + 31) & ~static_cast<size_t>(31);
+  // the largest item (dom y / z: 16 whole rows) must fit the shared memory of a CTA
+  const size_t slot = (static_cast<size_t>(g.nx + 2 * kPad) * kRows + 31) & ~static_cast<size_t>(31);
   return kStages * 4 * slot * sizeof(float) + 128 <= 232448;
 }
 
@@ -343,7 +361,7 @@ cudaError_t make_sweep_maps(const GridParams& g, float* Iring, float* Sring, Swe
                                  static_cast<cuuint64_t>(g.nv) * 4};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   const cuuint32_t W = static_cast<cuuint32_t>(g.nx + 2 * kPad);
-  const cuuint32_t boxes[3][4] = {{W, kBlk + 1, kBlk + 1, 1}, {W, 1, kRows, 1}, {W, kRows, 1, 1}};
+  const cuuint32_t boxes[3][4] = {{kXw, kBlk + 1, kBlk + 1, 1}, {W, 1, kRows, 1}, {W, kRows, 1, 1}};
   for (int c = 0; c < 3; ++c)
     for (int f = 0; f < 2; ++f) {
       CUtensorMap* m = reinterpret_cast<CUtensorMap*>(f == 0 ? out->I[c] : out->S[c]);
@@ -363,7 +381,8 @@ cudaError_t launch_class(const GridParams& g, const DirInfo* dirs, const int* dl
                          int first, int nsm, cudaStream_t st) {
   if (ndir == 0) return cudaSuccess;
   using Bx = Box<DOM>;
-  const size_t slot = (static_cast<size_t>(g.nx + 2 * kPad) * Bx::RY * Bx::RZ + 31) & ~static_cast<size_t>(31);
+  const size_t w = DOM == 0 ? kXw : g.nx + 2 * kPad;
+  const size_t slot = (w * Bx::RY * Bx::RZ + 31) & ~static_cast<size_t>(31);
   const size_t smem = kStages * 4 * slot * sizeof(float) + 128;  // + alignment slack
   CUtensorMap mI, mS;
   std::memcpy(&mI, maps.I[DOM], sizeof(CUtensorMap));

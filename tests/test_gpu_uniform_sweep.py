@@ -64,31 +64,34 @@ def test_uniform_forms_match_per_voxel_forms(precision, nside_scatter):
             np.testing.assert_allclose(got[k], base[k], rtol=1e-12, atol=0)
 
 
-@pytest.mark.parametrize("face", [0, 3, 4])
-def test_tma_sweep_matches_plain_sweep(face):
+@pytest.mark.parametrize("face,grid", [(0, (20, 12, 16)), (3, (20, 12, 16)), (4, (20, 12, 16)),
+                                       (1, (44, 10, 9)), (5, (44, 10, 9))])
+def test_tma_sweep_matches_plain_sweep(face, grid):
     """With a uniform refractive index, vacuum faces and nx a multiple of 4 the sweep stages
     its upwind planes through the TMA (one kernel per dominant-axis class); changing n in
     one unreachable corner voxel sends the step through the plain-load sweep.  The pulse
     enters through an x, y or z face so that each class sees the source face's inflow;
-    fields must agree bit for bit."""
+    nx = 44 gives the x-dominant items a full 32-voxel chunk and a ragged one.  Fields must
+    agree bit for bit."""
     P = _lib()
-    p = W.homogeneous(20, 12, 16, 4, 0.01, 2.0, steps=STEPS, tol=1e-6)
+    n = grid
+    p = W.homogeneous(n[0], n[1], n[2], 4, 0.01, 2.0, steps=STEPS, tol=1e-6)
     axis = face // 2
-    n = (20, 12, 16)
     uv = [a for a in range(3) if a != axis]
     p["source"] = dict(face=face, u_mm=n[uv[0]] / 2, v_mm=n[uv[1]] / 2, half_angle_deg=15.0,
                        pulse_steps=2, energy=1.0)
     fw = P.Forward(p)
     launches = fw.kernels_per_step()
+    form = fw.sweep_form()
     fw.close()
-    assert launches == 6  # three sweep classes, scatter, tallies, step counter
+    assert launches == 6 and form == "tma"  # three sweep classes, scatter, tallies, step counter
     base = _run(p)
     assert np.max(np.abs(base["I"])) > 0
     q = dict(p)
     q["nidx"] = p["nidx"].copy()
     q["nidx"][-1, -1, -1 if face % 2 == 0 else 0] = 1.3
     fw = P.Forward(q)
-    assert fw.kernels_per_step() == 4
+    assert fw.kernels_per_step() == 4 and fw.sweep_form() == "plain"
     fw.close()
     got = _run(q)
     for k in ("I", "S", "I1"):
