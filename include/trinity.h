@@ -149,6 +149,15 @@ int trinity_set_fresnel(trinity_ctx* ctx, int on);
  * first step. */
 int trinity_set_exact_solve(trinity_ctx* ctx, int on);
 
+/* Initial guess of each step's source iteration (Eq. 12, Section 2.4 steps 5-6):
+ *   mode = 1 (default): the linear extrapolation in time 2 S(n-1) - S(n-2) (S(n-1) at the
+ *            first stored level);
+ *   mode = 0: the previous level S(n-1), as Section 2.4 states it.
+ * The iteration converges to the same fixed point and stops by the same rule either way;
+ * the extrapolated guess starts closer to it, so fewer iterations are needed.
+ * TRINITY_E_INVALID for another mode; TRINITY_E_STATE after the first step. */
+int trinity_set_warm_start(trinity_ctx* ctx, int mode);
+
 /* Number of optics classes the exact solve uses (0 when it is off). */
 int trinity_exact_classes(const trinity_ctx* ctx, int* n);
 

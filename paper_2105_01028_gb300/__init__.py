@@ -82,6 +82,10 @@ class Forward:
         self._check(self.set_optics(prob["mua"], prob["mus"], prob["nidx"], prob["g"]))
         if prob.get("fresnel", False):
             self._check(self.L.trinity_set_fresnel(self.h, 1))
+        warm = prob.get("warm_start", "extrapolated")  # or "previous": S(n-1) as the paper states
+        if warm not in ("extrapolated", "previous"):
+            raise ValueError("warm_start must be 'extrapolated' or 'previous'")
+        self._check(self.L.trinity_set_warm_start(self.h, 1 if warm == "extrapolated" else 0))
         ex = prob.get("exact", False)
         if ex:  # True / "tc": tensor cores where the grid allows; "simt": FP32 SIMT form
             self._check(self.L.trinity_set_exact_solve(self.h, 2 if ex == "simt" else 1))

@@ -53,6 +53,7 @@ SIGNATURES = {
     "trinity_set_exact_solve": (c_int, [c_void_p, c_int]),
     "trinity_exact_classes": (c_int, [c_void_p, P_int]),
     "trinity_exact_form": (c_int, [c_void_p, P_int]),
+    "trinity_set_warm_start": (c_int, [c_void_p, c_int]),
     "trinity_interface_count": (c_int, [c_void_p, P_int]),
     "trinity_interface_entries": (c_int, [c_int, c_int, c_int, c_int, c_double, c_int, c_void_p,
                                           c_void_p, c_void_p, c_void_p, c_void_p, c_size_t,

@@ -823,6 +823,7 @@ int trinity_create_grid(const trinity_grid_desc* desc, void* cuda_stream, trinit
   }
   b1ds.resize(children.size());
   for (size_t k = 0; k < children.size(); ++k) b1ds[k] = static_cast<float>(ctx->lat.ds[children[k]]);
+  g.warm = 1;  // the iteration starts from 2 S(n-1) - S(n-2) (trinity_set_warm_start)
   ctx->g_s = g;
   ctx->g_s.na = ctx->na_s;
   ctx->g_s.e_scale = static_cast<float>(desc->h_mm * desc->h_mm * desc->h_mm / kC0 *
@@ -1067,6 +1068,15 @@ int trinity_set_exact_solve(trinity_ctx* ctx, int on) {
 int trinity_exact_classes(const trinity_ctx* ctx, int* n) {
   if (!ctx || !n) return TRINITY_E_INVALID;
   *n = ctx->exact ? ctx->n_xcls : 0;
+  return TRINITY_OK;
+}
+
+int trinity_set_warm_start(trinity_ctx* ctx, int mode) {
+  if (!ctx) return TRINITY_E_INVALID;
+  if (mode != 0 && mode != 1) return fail(ctx, TRINITY_E_INVALID, "warm start: mode must be 0 or 1");
+  if (ctx->locked) return fail(ctx, TRINITY_E_STATE, "the warm start must be chosen before the first step");
+  ctx->g.warm = mode;
+  ctx->g_s.warm = mode;
   return TRINITY_OK;
 }
 

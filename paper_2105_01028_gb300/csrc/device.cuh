@@ -27,6 +27,7 @@ struct GridParams {
   int periodic;
   int mirror;       // mirror faces: a ghost upwind sample reads its image (see sweep.cu)
   int hist_from;    // first valid time level: 0, or -4 with an initial state
+  int warm;         // initial guess of the source iteration: 0 S(n-1), 1 2 S(n-1) - S(n-2)
   int src_voxel;    // flat voxel index of the source spot, -1 if none
   int pulse_steps;
   float h;

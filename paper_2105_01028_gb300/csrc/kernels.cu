@@ -130,7 +130,9 @@ __global__ void __launch_bounds__(ScatterCfg<NA>::kThreads, 2)
   const float inv_nch = 1.0f / static_cast<float>(nch);
   const float ri = live ? rcorr[i] : 0.0f;
   const bool has_prev = (n - 1) >= g.hist_from;
+  const bool has_prev2 = g.warm != 0 && (n - 2) >= g.hist_from;  // linear extrapolation in time
   const size_t prev_off = (static_cast<size_t>(ring_slot(n - 1)) * g.na + (live ? i : 0)) * plane;
+  const size_t prev2_off = (static_cast<size_t>(ring_slot(n - 2)) * g.na + (live ? i : 0)) * plane;
 #pragma unroll
   for (int v = 0; v < kTile; ++v) {
     const int vv = v0 + v;
@@ -147,6 +149,7 @@ __global__ void __launch_bounds__(ScatterCfg<NA>::kThreads, 2)
     }
     b1[v] = bs * inv_nch;
     so[v] = (ok && has_prev) ? Sring[prev_off + vv] : 0.0f;
+    if (ok && has_prev2) so[v] = fmaf(2.0f, so[v], -Sring[prev2_off + vv]);
   }
   if (live) {
 #pragma unroll

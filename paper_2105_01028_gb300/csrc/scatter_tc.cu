@@ -357,7 +357,9 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
   const size_t plane = static_cast<size_t>(g.nv);
   const float s_glob = __uint_as_float(rs.smax[(n - 1) & 1]);
   const bool has_prev = (n - 1) >= g.hist_from;
+  const bool has_prev2 = g.warm != 0 && (n - 2) >= g.hist_from;  // linear extrapolation in time
   const size_t prev_base = static_cast<size_t>(ring_slot(n - 1)) * g.na * plane;
+  const size_t prev2_base = static_cast<size_t>(ring_slot(n - 2)) * g.na * plane;
   const size_t cur_base = static_cast<size_t>(ring_slot(n)) * g.na * plane;
   const int bxn = (g.nx + 7) >> 3, byn = (g.ny + 3) >> 2;
   const int ntiles = brick_tiles(g.nx, g.ny, g.nz);
@@ -473,8 +475,8 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
       den_s[tid] = static_cast<float>(NA) - (1.0f - e_s[tid]) * sb;
     }
 
-    // Warm start S(n-1): S_old -> TMEM, X_0 = Q + b1 S_old -> (X_hi, X_lo), and Q (read
-    // once) -> TMEM or registers.  The TMEM chunks go one at a time (not unrolled) so that
+    // Warm start S(n-1), or its linear extrapolation in time 2 S(n-1) - S(n-2): S_old ->
+    // TMEM, X_0 = Q + b1 S_old -> (X_hi, X_lo), and Q (read once) -> TMEM or registers.  The TMEM chunks go one at a time (not unrolled) so that
     // their loads are not batched.
     const auto warm = [&](int ch, float (&qc)[CH]) {
       const int c0 = cb + ch * CH;
@@ -483,6 +485,7 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
 #pragma unroll
       for (int j = 0; j < CH; ++j) {
         so[j] = (vin && has_prev) ? Sring[prev_base + static_cast<size_t>(c0 + j) * plane + v] : 0.0f;
+        if (vin && has_prev2) so[j] = fmaf(2.0f, so[j], -Sring[prev2_base + static_cast<size_t>(c0 + j) * plane + v]);
         qc[j] = vin ? __ldg(Q + static_cast<size_t>(c0 + j) * plane + v) : 0.0f;
       }
 #pragma unroll

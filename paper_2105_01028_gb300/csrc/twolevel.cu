@@ -39,6 +39,7 @@ struct Child {
 // kUniN / kUniMu: uniform refractive index / mu_t, so each child's delay split (m, f) /
 // exp(-x) and b0(x) are taken once per block (same FP32 operations on the same values).
 constexpr int kRowSweeps2 = 4;
+constexpr int kGroup = 4;  // children whose upwind loads are in flight together
 
 template <bool kUniN, bool kUniMu>
 __global__ void __launch_bounds__(256, 5) sweep2_kernel(GridParams g, const DirInfo* __restrict__ dirs,
@@ -124,67 +125,90 @@ __global__ void __launch_bounds__(256, 5) sweep2_kernel(GridParams g, const DirI
       const float mu = kUniMu ? 0.0f : __ldg(mut + v);
       const float nv_idx = kUniN ? 0.0f : __ldg(nidx + v);
       float acc = 0.0f;
-      for (int k = 0; k < nch; ++k) {
-        const Child& ch = cs[k];
-        const int dom = ch.dom, sgn = ch.sgn, nd = ch.nd, n0 = ch.n0, n1 = ch.n1;
-        const int pd = pick(dom, x, y, z), p0 = pick(ch.a0, x, y, z), p1 = pick(ch.a1, x, y, z);
-        const int kp = sgn > 0 ? pd : nd - 1 - pd;
-        int qd = pd - sgn;
-        int q0 = p0 - ch.off0[kp];
-        int q1 = p1 - ch.off1[kp];
-        int kind = 0;
-        if (g.periodic) {
-          qd = (qd + nd) % nd;
-          q0 = (q0 + n0) % n0;
-          q1 = (q1 + n1) % n1;
-        } else if (kp == 0) {
-          kind = 1;
-        } else if (q0 < 0 || q0 >= n0 || q1 < 0 || q1 >= n1) {
-          kind = 2;
-        }
-        int m;
-        float f;
-        if (kUniN) {
-          m = ch.m;
-          f = ch.f;
-        } else {
-          retarded_delay(ch.dc_hi, ch.dc_lo, nv_idx, m, f);
-          m = m < 1 ? 1 : (m > 3 ? 3 : m);  // the optics check keeps every delay in [1, 4)
-        }
-        const int L0 = n - m, L1 = n - m - 1;
-        float Iup = 0.0f, Sup = 0.0f;
-        if (kind == 0) {
-          const int u = qd * ch.sd + q0 * ch.s0 + q1 * ch.s1;  // < nv <= 2^30
-          const float* i0p = ch.ilev[m];
-          const float* i1p = ch.ilev[m + 1];
-          float i0 = 0.0f, i1 = 0.0f, s0v = 0.0f, s1v = 0.0f;
-          if (i0p) {
-            i0 = __ldg(i0p + u);
-            s0v = __ldg(slev_s[m] + u);
+      // children in groups of kGroup: the group's upwind loads are issued together, then
+      // its Q_f are formed and stored in the children table's order
+      for (int k0 = 0; k0 < nch; k0 += kGroup) {
+        float i0[kGroup], i1[kGroup], s0v[kGroup], s1v[kGroup], fw[kGroup];
+        int kind[kGroup], mg[kGroup];
+#pragma unroll
+        for (int j = 0; j < kGroup; ++j) {
+          i0[j] = i1[j] = s0v[j] = s1v[j] = 0.0f;
+          kind[j] = 3;
+          mg[j] = 1;
+          fw[j] = 0.0f;
+          const int k = k0 + j;
+          if (k >= nch) continue;
+          const Child& ch = cs[k];
+          const int dom = ch.dom, sgn = ch.sgn, nd = ch.nd, n0 = ch.n0, n1 = ch.n1;
+          const int pd = pick(dom, x, y, z), p0 = pick(ch.a0, x, y, z), p1 = pick(ch.a1, x, y, z);
+          const int kp = sgn > 0 ? pd : nd - 1 - pd;
+          int qd = pd - sgn;
+          int q0 = p0 - ch.off0[kp];
+          int q1 = p1 - ch.off1[kp];
+          int kd = 0;
+          if (g.periodic) {
+            qd = (qd + nd) % nd;
+            q0 = (q0 + n0) % n0;
+            q1 = (q1 + n1) % n1;
+          } else if (kp == 0) {
+            kd = 1;
+          } else if (q0 < 0 || q0 >= n0 || q1 < 0 || q1 >= n1) {
+            kd = 2;
           }
-          if (i1p) {
-            i1 = __ldg(i1p + u);
-            s1v = __ldg(slev_s[m + 1] + u);
+          int m;
+          float f;
+          if (kUniN) {
+            m = ch.m;
+            f = ch.f;
+          } else {
+            retarded_delay(ch.dc_hi, ch.dc_lo, nv_idx, m, f);
+            m = m < 1 ? 1 : (m > 3 ? 3 : m);  // the optics check keeps every delay in [1, 4)
           }
-          Iup = (1.0f - f) * i0 + f * i1;
-          Sup = (1.0f - f) * s0v + f * s1v;
-        } else if (kind == 1 && v == g.src_voxel && ch.src_amp != 0.0f) {
-          const float on0 = (L0 >= 0 && L0 < g.pulse_steps) ? 1.0f : 0.0f;
-          const float on1 = (L1 >= 0 && L1 < g.pulse_steps) ? 1.0f : 0.0f;
-          Iup = ch.src_amp * ((1.0f - f) * on0 + f * on1);
+          kind[j] = kd;
+          mg[j] = m;
+          fw[j] = f;
+          if (kd == 0) {
+            const int u = qd * ch.sd + q0 * ch.s0 + q1 * ch.s1;  // < nv <= 2^30
+            const float* i0p = ch.ilev[m];
+            const float* i1p = ch.ilev[m + 1];
+            if (i0p) {
+              i0[j] = __ldg(i0p + u);
+              s0v[j] = __ldg(slev_s[m] + u);
+            }
+            if (i1p) {
+              i1[j] = __ldg(i1p + u);
+              s1v[j] = __ldg(slev_s[m + 1] + u);
+            }
+          }
         }
-        float T, b0;
-        if (kUniMu) {
-          T = ch.T;
-          b0 = ch.b0;
-        } else {
-          const float xo = mu * ch.ds;
-          T = expf(-xo);
-          b0 = ray_b0(xo, T);
+#pragma unroll
+        for (int j = 0; j < kGroup; ++j) {
+          if (kind[j] == 3) break;
+          const Child& ch = cs[k0 + j];
+          const float f = fw[j];
+          float Iup = 0.0f, Sup = 0.0f;
+          if (kind[j] == 0) {
+            Iup = (1.0f - f) * i0[j] + f * i1[j];
+            Sup = (1.0f - f) * s0v[j] + f * s1v[j];
+          } else if (kind[j] == 1 && v == g.src_voxel && ch.src_amp != 0.0f) {
+            const int L0 = n - mg[j], L1 = n - mg[j] - 1;
+            const float on0 = (L0 >= 0 && L0 < g.pulse_steps) ? 1.0f : 0.0f;
+            const float on1 = (L1 >= 0 && L1 < g.pulse_steps) ? 1.0f : 0.0f;
+            Iup = ch.src_amp * ((1.0f - f) * on0 + f * on1);
+          }
+          float T, b0;
+          if (kUniMu) {
+            T = ch.T;
+            b0 = ch.b0;
+          } else {
+            const float xo = mu * ch.ds;
+            T = expf(-xo);
+            b0 = ray_b0(xo, T);
+          }
+          const float q = Iup * T + Sup * b0;
+          ch.qf[v] = q;
+          acc += q;
         }
-        const float q = Iup * T + Sup * b0;
-        ch.qf[v] = q;
-        acc += q;
       }
       qc[v] = acc * inv;
     }

@@ -94,6 +94,23 @@ def test_small_config_iteration_counts_plausible(small_run):
     assert np.all(out["iters"][2:] <= np.array(ref.iters_max)[2:] + 5)
 
 
+def test_warm_start_from_the_previous_level(small_run):
+    """The paper's initial guess S(n-1) instead of the default extrapolation 2 S(n-1) -
+    S(n-2): the same fixed point within the same bar, with more iterations per step."""
+    T = _gpu()
+    out, ref = small_run
+    prob = dict(W.config_small(steps=100, tol=GPU_TOL), warm_start="previous")
+    fwd = T.Forward(prob)
+    fwd.step(100)
+    _check_detectors(fwd.detectors(), ref.det, FP32_TOL)
+    assert _rel_peak(fwd.field(T.FIELD_I), ref.level("I")) <= FP32_TOL
+    assert _rel_peak(fwd.field(T.FIELD_S), ref.level("S")) <= FP32_TOL
+    prev_mean = fwd.iterations()[1]
+    fwd.close()
+    # steps 10..99: the light fills the box; the extrapolated guess needs fewer iterations
+    assert np.mean(out["iters_mean"][10:]) < np.mean(prev_mean[10:])
+
+
 def test_small_config_at_workload_tolerance(small_run):
     """At the workload's own tol = 1e-6 the GPU still lands within the FP32 bar of the
     converged solution (the stop rule bounds the error of each step's iterate by tol, and
