@@ -261,22 +261,21 @@ def workload_config(args, precision=None):
                                 if args.exact else "source iteration (Eq. 12)")}
 
 
-def run_serve(args):
+def serve_measure(args, n_burst, n_req, rates, seed=4):
     """Served stream (the served workload, a bounded number of requests): cubic grids of
     32..96 voxels, 48 or 192 directions, 500..1500 steps, log-normal random-field optics
     (workloads.served_stream / config_served).  First the capacity is measured: a burst of
-    --serve-burst requests submitted at once, solves/s over its makespan.  Then for each
-    rate factor in --rates a stream of --serve requests arrives as a Poisson process at
+    ``n_burst`` requests submitted at once, solves/s over its makespan.  Then for each
+    rate factor in ``rates`` a stream of ``n_req`` requests arrives as a Poisson process at
     that fraction of the capacity, each request submitted at its arrival time; reported
     per rate: solves/s over the makespan, p50/p99 latency (submission to detector curves on
     the host), aggregate updates/s and the largest number of concurrent solves."""
     import torch
     import paper_2105_01028_gb300 as T
-    torch.cuda.set_device(0)
 
-    def draw(n_req, seed, rate):
+    def draw(n, sd, rate):
         out = []
-        for k, r in enumerate(W.served_stream(n_req, seed=seed, rate_per_s=rate)):
+        for k, r in enumerate(W.served_stream(n, seed=sd, rate_per_s=rate)):
             p = W.config_served(r["n"], r["nside"], r["steps"], seed=r["seed"], precision=args.precision)
             p["steps"] = r["steps"]
             out.append((r["arrival_s"], p))
@@ -307,37 +306,47 @@ def run_serve(args):
             lat.append(ms)
         return time.perf_counter() - t0, np.array(lat)
 
-    burst = draw(args.serve_burst, 40, 1.0)
-    span, blat = play(burst, False)
-    capacity = len(burst) / span
-    c0 = srv.stats()["max_concurrent"]
-    results = []
-    for f in args.rates:
-        reqs = draw(args.serve, 4, f * capacity)
-        span, lat = play(reqs, True)
-        st = srv.stats()
-        results.append({"rate_factor": f, "arrival_rate_per_s": f * capacity, "requests": len(reqs),
-                        "solves_per_s": len(reqs) / span, "makespan_s": span,
-                        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                                       "max": float(np.max(lat))},
-                        "updates_per_s": updates(reqs) / span, "max_concurrent_so_far": st["max_concurrent"]})
+    with ClockSampler(0) as clk:
+        burst = draw(n_burst, 40, 1.0)
+        span, blat = play(burst, False)
+        capacity = len(burst) / span
+        c0 = srv.stats()["max_concurrent"]
+        results = []
+        for f in rates:
+            reqs = draw(n_req, seed, f * capacity)
+            span, lat = play(reqs, True)
+            st = srv.stats()
+            results.append({"rate_factor": f, "arrival_rate_per_s": f * capacity, "requests": len(reqs),
+                            "solves_per_s": len(reqs) / span, "makespan_s": span,
+                            "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                                           "p99": float(np.percentile(lat, 99)), "max": float(np.max(lat))},
+                            "updates_per_s": updates(reqs) / span, "max_concurrent_so_far": st["max_concurrent"]})
     stats = srv.stats()
     srv.close()
     head = results[-1]
-    line = {"metric": "served solves/s", "value": head["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+    return {"metric": "served solves/s", "value": head["solves_per_s"], "unit": "solves/s",
             "higher_is_better": True, "precision": args.precision, "data": "synthetic",
             "config": {"workload": "served stream: cubic 32..96 voxels @1mm, 48/192 dirs (p = 1/2), 500..1500 "
                                    "steps, log-normal GRF optics (sigma 0.3, correlation 5 mm, median mu_a "
                                    "0.01/mm, mu_s 10/mm), g 0.9, n 1.4; Poisson arrivals at the stated "
                                    "fractions of the measured capacity; %d requests per rate (bounded "
-                                   "sample of the 2000-request stream)" % args.serve,
+                                   "sample of the 2000-request stream)" % n_req,
                        "slots": args.slots, "steps_per_slice": 32},
             "capacity": {"solves_per_s": capacity, "burst_requests": len(burst), "makespan_s": len(burst) / capacity,
                          "updates_per_s": updates(burst) * capacity / len(burst), "max_concurrent": c0,
                          "burst_latency_ms": {"p50": float(np.percentile(blat, 50)),
                                               "p99": float(np.percentile(blat, 99))}},
             "rates": results, "latency_ms": head["latency_ms"],
-            "max_concurrent": stats["max_concurrent"], "completed": stats["completed"]}
+            "max_concurrent": stats["max_concurrent"], "completed": stats["completed"], "clocks": clk.summary()}
+
+
+def run_serve(args):
+    """The served stream alone (--serve N): capacity from a burst of --serve-burst requests,
+    then N requests per rate factor in --rates."""
+    import torch
+    torch.cuda.set_device(0)
+    line = serve_measure(args, args.serve_burst, args.serve, args.rates)
+    line["n_gpus"] = 1
     print(json.dumps(line))
 
 
@@ -470,27 +479,43 @@ def run_adjoint(args):
     print(json.dumps(line))
 
 
-def kernel_roofline(nv, na, na_s, kms, kp, k_mean, precision, pk, exact=False):
+def kernel_roofline(nv, na, na_s, kms, kp, k_mean, precision, pk, exact=None):
     """Per-kernel times (ms per step) and the roofline object of the dominant kernel from
-    ``kp`` profiled steps (``kms``: summed ms of sweep, source function, tallies)."""
+    ``kp`` profiled steps (``kms``: summed ms of sweep, source function, tallies).
+    ``exact``: None (the source iteration), "tc" or "simt" (the exact solve's form)."""
     hbm = pk["hbm_gbs"]
     sweep_bytes = nv * na * 20 + nv * 8  # I,S at two levels read (16 B), Q written (4 B); optics
     scat_bytes = nv * na_s * 16 + nv * 12  # Q, S(n-1) read, I, S written; optics
     scat_flops = 2.0 * na_s * na_s * nv * (1.0 if exact else k_mean)
     per = [kms[0] / kp, kms[1] / kp, kms[2] / kp]
     tot = sum(per)
-    if precision == "bf16" and not exact:
-        s_bound, s_peak = "tensor", pk.get("bf16_tflops_sustained", 1700.0)
+    s_name = ("exact_" + ("tc" if exact == "tc" else "fp32")) if exact else "scatter_" + precision
+    extra = {}
+    if exact == "tc":
+        # one product per voxel, HBM-bound: Q in, I and S out (12 B per update) + class,
+        # index and optics bytes per voxel; the tensor pipe runs three TF32 products
+        s_bound, s_peak, s_unit = "hbm", hbm, "GB/s"
+        x_bytes = nv * na_s * 12 + nv * 5
+        s_ach = x_bytes / (per[1] * 1e-3) / 1e9
+        tf32_peak = pk.get("bf16_tflops", 1900.0) * 1.1 / 2.25  # measured BF16 x nominal TF32/BF16
+        tc_tf = 3 * scat_flops / (per[1] * 1e-3) / 1e12
+        extra = {"algorithmic_bytes": x_bytes, "tensor_tflops_3xtf32": tc_tf,
+                 "tensor_frac_of_tf32": tc_tf / tf32_peak,
+                 "tf32_peak": "%.0f TFLOP/s (measured BF16 burst x 1.1/2.25 nominal ratio)" % tf32_peak}
     else:
-        s_bound, s_peak = "alu", fp32_peak_tflops(pk)
-    s_ach = scat_flops / (per[1] * 1e-3) / 1e12
+        if precision == "bf16" and not exact:
+            s_bound, s_peak = "tensor", pk.get("bf16_tflops_sustained", 1700.0)
+        else:
+            s_bound, s_peak = "alu", fp32_peak_tflops(pk)
+        s_unit = "TFLOP/s"
+        s_ach = scat_flops / (per[1] * 1e-3) / 1e12
     w_ach = sweep_bytes / (per[0] * 1e-3) / 1e9
     kernels = [
         {"name": "sweep", "ms": per[0], "share": per[0] / tot, "bound": "hbm", "achieved": w_ach,
          "peak": hbm, "unit": "GB/s", "frac": w_ach / hbm, "algorithmic_bytes": sweep_bytes},
-        {"name": "exact_fp32" if exact else "scatter_" + precision, "ms": per[1], "share": per[1] / tot,
-         "bound": s_bound, "achieved": s_ach, "peak": s_peak, "unit": "TFLOP/s", "frac": s_ach / s_peak,
-         "algorithmic_flops": scat_flops, "hbm_gbs": scat_bytes / (per[1] * 1e-3) / 1e9},
+        dict({"name": s_name, "ms": per[1], "share": per[1] / tot,
+              "bound": s_bound, "achieved": s_ach, "peak": s_peak, "unit": s_unit, "frac": s_ach / s_peak,
+              "algorithmic_flops": scat_flops, "hbm_gbs": scat_bytes / (per[1] * 1e-3) / 1e9}, **extra),
         {"name": "tally+advance", "ms": per[2], "share": per[2] / tot},
     ]
     dom = max(kernels[:2], key=lambda k: k["ms"])
@@ -526,11 +551,13 @@ def measure_window(T, torch, prob, stream, spinup, warmup, steps, what):
     _, k_it_mean = fwd.iterations()
     executed = fwd.executed_iterations()[first:first + steps]
     kps = fwd.kernels_per_step()
+    xform = fwd.exact_form()
     fwd.close()
     nv = prob["nx"] * prob["ny"] * prob["nz"]
     na = 12 * prob["nside"] ** 2
     prec = prob.get("precision", "fp32")
-    kernels, roof = kernel_roofline(nv, na, na, kms, kp, float(np.mean(k_it_mean[-kp:])), prec, peaks())
+    kernels, roof = kernel_roofline(nv, na, na, kms, kp, float(np.mean(k_it_mean[-kp:])), prec, peaks(),
+                                    exact=xform)
     return {"workload": what, "precision": prec, "value": nv * na * steps / (ms * 1e-3), "unit": "updates/s",
             "ms_per_step": ms / steps, "window": "time steps %d..%d" % (first, first + steps - 1),
             "iterations": {"mean": float(np.mean(it_mean[first:first + steps])),
@@ -599,6 +626,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--grid", type=int, nargs=3, default=[96, 96, 64], metavar=("NX", "NY", "NZ"),
                     help="slab size (smaller grids are for profiling captures only)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served-stream sub-object of the default line")
     ap.add_argument("--serve", type=int, default=0, metavar="N",
                     help="run the served stream with N requests per rate instead of the slab")
     ap.add_argument("--serve-burst", type=int, default=12,
@@ -688,6 +716,7 @@ def main():
     k_it_max, k_it_mean = fwd.iterations()
     k_mean = float(np.mean(k_it_mean[-kp:]))
     executed = fwd.executed_iterations()[first:first + args.steps]
+    k_exec = float(np.mean(fwd.executed_iterations()[-kp:]))  # the profiled steps
     kps = fwd.kernels_per_step()
     xform = fwd.exact_form()
     sweep_kernel = {"plain": "sweep_kernel", "tma": "sweep_tma_kernel", "two-level": "sweep2_kernel"}[fwd.sweep_form()]
@@ -727,6 +756,12 @@ def main():
         tc_extra = {"algorithmic_bytes": x_bytes, "tensor_tflops_3xtf32": tc_tf,
                     "tensor_frac_of_tf32": tc_tf / tf32_peak,
                     "tf32_peak": "%.0f TFLOP/s (measured BF16 burst x 1.1/2.25 nominal ratio)" % tf32_peak}
+    elif args.precision == "bf16" and not args.exact and k_exec > 0:
+        # what the tensor pipe executes: every tile iterates until its slowest voxel stops,
+        # and X is carried as two BF16 terms (two MMAs per iteration)
+        ex_tf = 2 * 2.0 * na_s * na_s * nv * k_exec / (per[1] * 1e-3) / 1e12
+        tc_extra = {"executed_iterations_per_voxel": k_exec, "tensor_tflops_executed": ex_tf,
+                    "tensor_frac_executed": ex_tf / s_peak}
     w_ach = sweep_bytes / (per[0] * 1e-3) / 1e9
     kernels = [
         {"name": "sweep", "ms": per[0], "share": per[0] / tot, "bound": "hbm",
@@ -795,6 +830,14 @@ def main():
             "heterogeneous phantom 128x128x96 @1mm, 192 dirs, slab optics, air cylinder r 5 mm (n 1) with "
             "Fresnel refraction/reflection at its wall, 3 absorbing spheres r 4/6/8 mm (mu_a x2/x3.5/x5), "
             "-x face pulse, 8 detectors; BF16 scatter, FP32 sweep, general per-voxel kernel forms")
+        pe = W.config_slab(steps=total, precision="fp32", nx=nx, ny=ny, nz=nz)
+        pe["exact"] = True
+        line["exact"] = measure_window(
+            T, torch, pe, stream, args.spinup, args.warmup, args.steps,
+            "the same slab and time window with the exact per-voxel source function S = M Q (one optics "
+            "class) on the tensor cores: three TF32 products, FP32 accumulation")
+    if plain and not args.no_configs and not args.no_serve and rank == 0:
+        line["served"] = serve_measure(args, 8, 12, [0.8])
 
     if args.two_level or args.exact:
         line["cpu_baseline"] = None

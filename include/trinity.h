@@ -151,8 +151,9 @@ int trinity_set_exact_solve(trinity_ctx* ctx, int on);
 
 /* Initial guess of each step's source iteration (Eq. 12, Section 2.4 steps 5-6):
  *   mode = 1 (default): the linear extrapolation in time 2 S(n-1) - S(n-2) (S(n-1) at the
- *            first stored level);
- *   mode = 0: the previous level S(n-1), as Section 2.4 states it.
+ *            first stored level); the adjoint's transposed solve likewise starts from
+ *            2 y(n+1) - y(n+2) of the two reverse steps before it;
+ *   mode = 0: the previous level S(n-1), as Section 2.4 states it (and y(n+1)).
  * The iteration converges to the same fixed point and stops by the same rule either way;
  * the extrapolated guess starts closer to it, so fewer iterations are needed.
  * TRINITY_E_INVALID for another mode; TRINITY_E_STATE after the first step. */

@@ -116,7 +116,8 @@ __global__ void adj_inject_kernel(const int* __restrict__ det_vox, const int* __
 // forward FP32 kernel (a CTA owns 16 voxels, thread i owns direction i, blocked sums of
 // P X with the diagonal row-sum correction r_i, y = (1 - eps) (P X + r X), the same stop
 // rule with a stall exit, the same isotropic rebalance after each plain update) with
-// q = Sbar_n + b1 Ibar_n and a warm start from the previous reverse step's y.  The
+// q = Sbar_n + b1 Ibar_n and a warm start from the previous reverse step's y, or (Y2
+// given and ``extrap``) its linear extrapolation 2 y(n+1) - y(n+2).  The
 // epilogue writes Qbar = Ibar_n + y, clears the consumed adjoint
 // level, and adds the voxel's dL/da and the b1 part of dL/dmu_t to the FP64 sums.
 // ----------------------------------------------------------------------------------------
@@ -136,7 +137,8 @@ __global__ void __launch_bounds__(AdjCfg<NA>::kThreads, 2)
                             const float* __restrict__ mut, const float* __restrict__ eps,
                             float* __restrict__ Ib_n, float* __restrict__ Sb_n,
                             const float* __restrict__ I_n, const float* __restrict__ S_n,
-                            float* __restrict__ Y, float* __restrict__ Qb, double* __restrict__ gA,
+                            float* __restrict__ Y, float* __restrict__ Y2, int extrap,
+                            float* __restrict__ Qb, double* __restrict__ gA,
                             double* __restrict__ gmut, float tol, int max_iters,
                             const unsigned* __restrict__ yglob_prev, unsigned* ymax_cur,
                             int* nonconv, unsigned long long* iters_sum) {
@@ -187,6 +189,7 @@ __global__ void __launch_bounds__(AdjCfg<NA>::kThreads, 2)
     b1[v] = ok ? ray_b1(xo, expf(-xo)) : 0.0f;
     q[v] = ok ? fmaf(b1[v], Ib_n[row + vv], Sb_n[row + vv]) : 0.0f;
     so[v] = ok ? Y[row + vv] : 0.0f;
+    if (ok && extrap) so[v] = fmaf(2.0f, so[v], -Y2[row + vv]);
   }
   if (live) {
 #pragma unroll
@@ -327,6 +330,7 @@ __global__ void __launch_bounds__(AdjCfg<NA>::kThreads, 2)
       const size_t o = row + vv;
       const float qbar = Ib_n[o] + so[v];
       Qb[o] = qbar;
+      if (Y2) Y2[o] = Y[o];  // this thread read Y[o] in the prologue; it still holds y(n+1)
       Y[o] = so[v];
       Ib_n[o] = 0.0f;
       Sb_n[o] = 0.0f;
@@ -498,14 +502,16 @@ cudaError_t launch_adj_inject(const int* det_vox, const int* det_dir, const floa
 cudaError_t launch_adj_scatter_fp32(const GridParams& g, const DirInfo* dirs, const float* P,
                                     const float* rcorr, const float* mut, const float* eps,
                                     float* Ib_n, float* Sb_n, const float* I_n, const float* S_n,
-                                    float* Y, float* Qb, double* gA, double* gmut, float tol,
+                                    float* Y, float* Y2, int extrap, float* Qb, double* gA, double* gmut,
+                                    float tol,
                                     int max_iters, const unsigned* yglob_prev, unsigned* ymax_cur,
                                     int* nonconv, unsigned long long* iters_sum, cudaStream_t st) {
   const int tiles = (g.nv + kTile - 1) / kTile;
 #define TRINITY_ADJ_CASE(NA)                                                                   \
   case NA:                                                                                     \
     adj_scatter_fp32_kernel<NA><<<tiles, AdjCfg<NA>::kThreads, 0, st>>>(                       \
-        g.nv, dirs, g.ds_max, P, rcorr, mut, eps, Ib_n, Sb_n, I_n, S_n, Y, Qb, gA, gmut, tol,   \
+        g.nv, dirs, g.ds_max, P, rcorr, mut, eps, Ib_n, Sb_n, I_n, S_n, Y, Y2, extrap, Qb, gA,  \
+        gmut, tol,                                                                             \
         max_iters, yglob_prev, ymax_cur, nonconv, iters_sum);                                  \
     break;
   switch (g.na) {

@@ -132,7 +132,7 @@ struct trinity_ctx {
   unsigned* d_ckpt_smax = nullptr;  // [n_ckpt] max |S(c-1)|
   float *d_stI = nullptr, *d_stS = nullptr;  // segment store [every + 4][na][nv]
   float *d_aI = nullptr, *d_aS = nullptr;    // adjoint levels Ibar, Sbar [5][na][nv]
-  float *d_Qb = nullptr, *d_Y = nullptr;     // Qbar and the warm start of the transposed solve
+  float *d_Qb = nullptr, *d_Y = nullptr;     // Qbar; [2] y of the last two reverse steps (warm start)
   double *d_gA = nullptr, *d_gmut = nullptr, *d_gmua = nullptr, *d_gmus = nullptr, *d_G = nullptr;
   unsigned* d_ymax = nullptr;       // [2] max |y| of the last two reverse steps
   int* d_adj_nonconv = nullptr;
@@ -480,7 +480,7 @@ size_t adjoint_bytes(size_t na, size_t nv, int nsteps, int every, int ndet_bins)
   const size_t nck = static_cast<size_t>((nsteps + every - 1) / every) + 1;
   size_t b = nck * 8 * lvl + nck * sizeof(unsigned);  // checkpoints
   b += static_cast<size_t>(every + 4) * 2 * lvl;      // segment store
-  b += 12 * lvl;                                      // adjoint levels, Qbar, warm start
+  b += 13 * lvl;                                      // adjoint levels, Qbar, two warm-start levels
   b += 4 * nv * sizeof(double);                       // gradient sums and outputs
   b += static_cast<size_t>(ndet_bins) * 2 * sizeof(double) +
        static_cast<size_t>(nsteps) * (2 * sizeof(double) + sizeof(int) + sizeof(unsigned long long));
@@ -1421,7 +1421,7 @@ int adjoint_impl(trinity_ctx* ctx, const double* dL_dE, size_t n, double* grad_m
     bool ok = dalloc(&ctx->d_stI, static_cast<size_t>(every + 4) * lvl) == cudaSuccess &&
               dalloc(&ctx->d_stS, static_cast<size_t>(every + 4) * lvl) == cudaSuccess &&
               dalloc(&ctx->d_aI, kRing * lvl) == cudaSuccess && dalloc(&ctx->d_aS, kRing * lvl) == cudaSuccess &&
-              dalloc(&ctx->d_Qb, lvl) == cudaSuccess && dalloc(&ctx->d_Y, lvl) == cudaSuccess &&
+              dalloc(&ctx->d_Qb, lvl) == cudaSuccess && dalloc(&ctx->d_Y, 2 * lvl) == cudaSuccess &&
               dalloc(&ctx->d_gA, nv) == cudaSuccess && dalloc(&ctx->d_gmut, nv) == cudaSuccess &&
               dalloc(&ctx->d_gmua, nv) == cudaSuccess && dalloc(&ctx->d_gmus, nv) == cudaSuccess &&
               dalloc(&ctx->d_G, ndb) == cudaSuccess && dalloc(&ctx->d_ymax, 2) == cudaSuccess &&
@@ -1443,7 +1443,7 @@ int adjoint_impl(trinity_ctx* ctx, const double* dL_dE, size_t n, double* grad_m
                        ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemsetAsync(ctx->d_aI, 0, kRing * lvl * 4, ctx->stream));
   CK(cudaMemsetAsync(ctx->d_aS, 0, kRing * lvl * 4, ctx->stream));
-  CK(cudaMemsetAsync(ctx->d_Y, 0, lvl * 4, ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_Y, 0, 2 * lvl * 4, ctx->stream));  // y(n+1) and y(n+2) of the warm start
   CK(cudaMemsetAsync(ctx->d_gA, 0, nv * 8, ctx->stream));
   CK(cudaMemsetAsync(ctx->d_gmut, 0, nv * 8, ctx->stream));
   CK(cudaMemsetAsync(ctx->d_ymax, 0, 2 * sizeof(unsigned), ctx->stream));
@@ -1514,7 +1514,9 @@ int adjoint_impl(trinity_ctx* ctx, const double* dL_dE, size_t n, double* grad_m
       CK(launch_adj_inject(ctx->d_det_vox, ctx->d_det_dir, ctx->d_det_w, ctx->d_det_id, ctx->n_det_entries,
                            ctx->d_G, ctx->nbins, bin, aI_n, g.nv, ctx->d_ymax + (lev & 1), ctx->stream));
       CK(launch_adj_scatter_fp32(g, ctx->d_dirs, ctx->P32, ctx->d_rcorr32, ctx->mut, ctx->eps, aI_n, aS_n,
-                                 ctx->d_stI + here, ctx->d_stS + here, ctx->d_Y, ctx->d_Qb, ctx->d_gA,
+                                 ctx->d_stI + here, ctx->d_stS + here, ctx->d_Y,
+                                 ctx->g.warm ? ctx->d_Y + lvl : nullptr, ctx->g.warm && lev <= N - 3 ? 1 : 0,
+                                 ctx->d_Qb, ctx->d_gA,
                                  ctx->d_gmut, tol, ctx->desc.max_iters, ctx->d_ymax + ((lev + 1) & 1),
                                  ctx->d_ymax + (lev & 1), ctx->d_adj_nonconv, ctx->d_adj_iters,
                                  ctx->stream));

@@ -179,8 +179,8 @@ cudaError_t launch_adj_inject(const int* det_vox, const int* det_dir, const floa
 cudaError_t launch_adj_scatter_fp32(const GridParams& g, const DirInfo* dirs, const float* P,
                                     const float* rcorr, const float* mut, const float* eps,
                                     float* Ib_n, float* Sb_n, const float* I_n, const float* S_n,
-                                    float* Y, float* Qb, double* gA, double* gmut, float tol,
-                                    int max_iters, const unsigned* yglob_prev, unsigned* ymax_cur,
+                                    float* Y, float* Y2, int extrap, float* Qb, double* gA, double* gmut,
+                                    float tol, int max_iters, const unsigned* yglob_prev, unsigned* ymax_cur,
                                     int* nonconv, unsigned long long* iters_sum, cudaStream_t st);
 cudaError_t launch_adj_push(const GridParams& g, const DirInfo* dirs, const int8_t* offs,
                             const float* stI, const float* stS, int lev_base, int n,

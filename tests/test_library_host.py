@@ -55,11 +55,12 @@ def test_footprint_and_invalid_descriptions():
 
 def test_adjoint_footprint():
     # 64^3, 192 directions, 800 steps, checkpoints every 50: 17 checkpoints of 8 levels,
-    # a 54-level store of I and S, 12 more levels for the reverse sweep
+    # a 54-level store of I and S, 13 more levels for the reverse sweep (adjoint ring of I
+    # and S, Qbar, two warm-start levels)
     d = _lib.GridDesc(64, 64, 64, 1.0, 4, 0.5, 1.4, 0, 0, 1e-6, 2000)
     fb = T.lib().trinity_adjoint_footprint_bytes(ctypes.byref(d), 800, 50, 8, 202)
     lvl = 64 ** 3 * 192 * 4
-    assert (17 * 8 + 54 * 2 + 12) * lvl <= fb <= (17 * 8 + 54 * 2 + 12) * lvl + 64 * 2 ** 20
+    assert (17 * 8 + 54 * 2 + 13) * lvl <= fb <= (17 * 8 + 54 * 2 + 13) * lvl + 64 * 2 ** 20
     assert T.lib().trinity_adjoint_footprint_bytes(ctypes.byref(d), 0, 50, 8, 202) == 0
     assert T.lib().trinity_adjoint_footprint_bytes(ctypes.byref(d), 800, 0, 8, 202) == 0
 
