@@ -84,6 +84,8 @@ struct trinity_ctx {
   // TMA-staged sweep (uniform n, vacuum faces, nx % 4 == 0): tensor maps of the rings and
   // the directions of each dominant-axis class
   bool tma = false;
+  cudaStream_t side[2] = {nullptr, nullptr};  // the TMA sweep's classes run concurrently
+  cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
   SweepMaps maps{};
   int* d_dlist[3] = {nullptr, nullptr, nullptr};
   int ndir[3] = {0, 0, 0};
@@ -532,8 +534,17 @@ int enqueue_transport(trinity_ctx* ctx, const RunState& rs) {
                      ctx->mut, ctx->nidx, ctx->Q, ctx->Qc, rs, ctx->stream));
   } else if (ctx->tma && g.n_u >= 1.0f) {
     const int* dl[3] = {ctx->d_dlist[0], ctx->d_dlist[1], ctx->d_dlist[2]};
+    // the three dominant-axis classes on the context's stream and two side streams (forked
+    // and joined by events, so a captured step holds them as parallel graph nodes)
+    const cudaStream_t st3[3] = {ctx->stream, ctx->side[0], ctx->side[1]};
+    CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
+    for (int k = 0; k < 2; ++k) CK(cudaStreamWaitEvent(ctx->side[k], ctx->ev_fork, 0));
     CK(launch_sweep_tma(g, ctx->d_dirs, dl, ctx->ndir, ctx->d_offs, ctx->d_hsh, ctx->maps, ctx->mut, ctx->Q, rs,
-                        ctx->stream));
+                        st3));
+    for (int k = 0; k < 2; ++k) {
+      CK(cudaEventRecord(ctx->ev_join[k], ctx->side[k]));
+      CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join[k], 0));
+    }
   } else {
     CK(launch_sweep(g, ctx->d_dirs, ctx->d_offs, ctx->I, ctx->S, ctx->mut, ctx->nidx, ctx->d_refl, ctx->Q, rs,
                     ctx->stream));
@@ -926,6 +937,10 @@ int trinity_create_grid(const trinity_grid_desc* desc, void* cuda_stream, trinit
           if (ctx->lat.off[(static_cast<size_t>(d) * 2 + j) * g.nmax + k] > 0) hsh[d] |= static_cast<int8_t>(1 << j);
     ok = ok && dalloc(&ctx->d_hsh, hsh.size()) == cudaSuccess &&
          cudaMemcpy(ctx->d_hsh, hsh.data(), hsh.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    for (int k = 0; k < 2 && ok; ++k)
+      ok = cudaStreamCreateWithFlags(&ctx->side[k], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&ctx->ev_join[k], cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) == cudaSuccess;
     ctx->tma = ok;
     if (!ok) cudaGetLastError();  // fall back to the plain-load sweep
   }
@@ -1781,6 +1796,11 @@ void trinity_destroy(trinity_ctx* ctx) {
   cudaFree(ctx->d_tmask);
   for (int c = 0; c < 3; ++c) cudaFree(ctx->d_dlist[c]);
   cudaFree(ctx->d_hsh);
+  for (int k = 0; k < 2; ++k) {
+    if (ctx->side[k]) cudaStreamDestroy(ctx->side[k]);
+    if (ctx->ev_join[k]) cudaEventDestroy(ctx->ev_join[k]);
+  }
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   void* bufs[] = {ctx->I,         ctx->S,          ctx->Q,           ctx->mut,       ctx->eps,
                   ctx->nidx,      ctx->P32,        ctx->Pbf,         ctx->d_dirs,    ctx->d_offs,

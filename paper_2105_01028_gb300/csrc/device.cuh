@@ -155,7 +155,7 @@ bool sweep_tma_supported(const GridParams& g);
 cudaError_t make_sweep_maps(const GridParams& g, float* Iring, float* Sring, SweepMaps* out);
 cudaError_t launch_sweep_tma(const GridParams& g, const DirInfo* dirs, const int* const dlist[3],
                              const int ndir[3], const int8_t* offs, const int8_t* hsh, const SweepMaps& maps,
-                             const float* mut, float* Q, RunState rs, cudaStream_t st);
+                             const float* mut, float* Q, RunState rs, const cudaStream_t st[3]);
 cudaError_t launch_energy_density(const GridParams& g, const float* I, const float* nidx, float scale, float* u,
                                   cudaStream_t st);
 cudaError_t launch_interface(int nvox, int na, const int* vox, const int* rowptr, const int* src,

@@ -403,7 +403,7 @@ cudaError_t launch_class(const GridParams& g, const DirInfo* dirs, const int* dl
 
 cudaError_t launch_sweep_tma(const GridParams& g, const DirInfo* dirs, const int* const dlist[3],
                              const int ndir[3], const int8_t* offs, const int8_t* hsh, const SweepMaps& maps,
-                             const float* mut, float* Q, RunState rs, cudaStream_t st) {
+                             const float* mut, float* Q, RunState rs, const cudaStream_t st[3]) {
   static int nsm = 0;
   if (nsm == 0) {
     int dev = 0;
@@ -413,9 +413,11 @@ cudaError_t launch_sweep_tma(const GridParams& g, const DirInfo* dirs, const int
   }
   // the first class launched (with directions) also clears this step's max |S| and work counter
   const int f2 = ndir[2] > 0, f1 = !f2 && ndir[1] > 0, f0 = !f2 && !f1;
-  cudaError_t e = launch_class<2>(g, dirs, dlist[2], ndir[2], offs, hsh, maps, mut, Q, rs, f2, nsm, st);
-  if (e == cudaSuccess) e = launch_class<1>(g, dirs, dlist[1], ndir[1], offs, hsh, maps, mut, Q, rs, f1, nsm, st);
-  if (e == cudaSuccess) e = launch_class<0>(g, dirs, dlist[0], ndir[0], offs, hsh, maps, mut, Q, rs, f0, nsm, st);
+  // the classes write disjoint planes of Q and only read the rings: st[k] may run them
+  // concurrently (the caller joins the streams before the next kernel)
+  cudaError_t e = launch_class<2>(g, dirs, dlist[2], ndir[2], offs, hsh, maps, mut, Q, rs, f2, nsm, st[0]);
+  if (e == cudaSuccess) e = launch_class<1>(g, dirs, dlist[1], ndir[1], offs, hsh, maps, mut, Q, rs, f1, nsm, st[1]);
+  if (e == cudaSuccess) e = launch_class<0>(g, dirs, dlist[0], ndir[0], offs, hsh, maps, mut, Q, rs, f0, nsm, st[2]);
   return e;
 }
 
