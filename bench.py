@@ -479,13 +479,28 @@ def run_adjoint(args):
     print(json.dumps(line))
 
 
+def iteration_bound(flops, nbytes, ms, c_bound, c_ach, c_peak, hbm):
+    """Roofline of a source-iteration kernel: its algorithmic FLOP per algorithmic byte
+    against the ridge point (compute peak / HBM peak) decides whether the compute or the
+    HBM roofline bounds it; both fractions are reported."""
+    ai = flops / nbytes
+    ridge = c_peak * 1e12 / (hbm * 1e9)
+    m_ach = nbytes / (ms * 1e-3) / 1e9
+    extra = {"arithmetic_intensity": ai, "ridge_flop_per_byte": ridge, "algorithmic_bytes": nbytes,
+             "compute_frac": c_ach / c_peak, "hbm_frac": m_ach / hbm}
+    if ai >= ridge:
+        return c_bound, c_ach, c_peak, "TFLOP/s", extra
+    return "hbm", m_ach, hbm, "GB/s", extra
+
+
 def kernel_roofline(nv, na, na_s, kms, kp, k_mean, precision, pk, exact=None):
     """Per-kernel times (ms per step) and the roofline object of the dominant kernel from
     ``kp`` profiled steps (``kms``: summed ms of sweep, source function, tallies).
     ``exact``: None (the source iteration), "tc" or "simt" (the exact solve's form)."""
     hbm = pk["hbm_gbs"]
     sweep_bytes = nv * na * 20 + nv * 8  # I,S at two levels read (16 B), Q written (4 B); optics
-    scat_bytes = nv * na_s * 16 + nv * 12  # Q, S(n-1) read, I, S written; optics
+    # Q, S(n-1), S(n-2) read (the extrapolated start), I and S written; optics
+    scat_bytes = nv * na_s * 20 + nv * 12
     scat_flops = 2.0 * na_s * na_s * nv * (1.0 if exact else k_mean)
     per = [kms[0] / kp, kms[1] / kp, kms[2] / kp]
     tot = sum(per)
@@ -509,6 +524,9 @@ def kernel_roofline(nv, na, na_s, kms, kp, k_mean, precision, pk, exact=None):
             s_bound, s_peak = "alu", fp32_peak_tflops(pk)
         s_unit = "TFLOP/s"
         s_ach = scat_flops / (per[1] * 1e-3) / 1e12
+        if not exact:
+            s_bound, s_ach, s_peak, s_unit, extra = iteration_bound(scat_flops, scat_bytes, per[1], s_bound,
+                                                                    s_ach, s_peak, hbm)
     w_ach = sweep_bytes / (per[0] * 1e-3) / 1e9
     kernels = [
         {"name": "sweep", "ms": per[0], "share": per[0] / tot, "bound": "hbm", "achieved": w_ach,
@@ -733,7 +751,8 @@ def main():
         # levels and the coarse mean Q once per coarse update
         sweep_bytes = nv * na * 12 + nv * na_s * 12 + nv * 8
     fin_bytes = nv * na * 8 + nv * na_s * 4 if nch > 1 else 0  # refine: Q_f in, I_f out, S_c in
-    scat_bytes = nv * na_s * 16 + nv * 12  # Q, S(n-1) read, I, S written; optics
+    # Q, S(n-1), S(n-2) read (the extrapolated start), I and S written; optics
+    scat_bytes = nv * na_s * 20 + nv * 12
     scat_flops = 2.0 * na_s * na_s * nv * k_mean  # angular sum per voxel per iteration
     per = [kms[0] / kp, kms[1] / kp, kms[2] / kp]
     tot = sum(per)
@@ -756,12 +775,16 @@ def main():
         tc_extra = {"algorithmic_bytes": x_bytes, "tensor_tflops_3xtf32": tc_tf,
                     "tensor_frac_of_tf32": tc_tf / tf32_peak,
                     "tf32_peak": "%.0f TFLOP/s (measured BF16 burst x 1.1/2.25 nominal ratio)" % tf32_peak}
-    elif args.precision == "bf16" and not args.exact and k_exec > 0:
-        # what the tensor pipe executes: every tile iterates until its slowest voxel stops,
-        # and X is carried as two BF16 terms (two MMAs per iteration)
-        ex_tf = 2 * 2.0 * na_s * na_s * nv * k_exec / (per[1] * 1e-3) / 1e12
-        tc_extra = {"executed_iterations_per_voxel": k_exec, "tensor_tflops_executed": ex_tf,
-                    "tensor_frac_executed": ex_tf / s_peak}
+    elif not args.exact:
+        c_peak = s_peak
+        s_bound, s_ach, s_peak, s_unit, tc_extra = iteration_bound(scat_flops, scat_bytes, per[1], s_bound, s_ach,
+                                                                   s_peak, hbm)
+        if args.precision == "bf16" and k_exec > 0:
+            # what the tensor pipe executes: every tile iterates until its slowest voxel
+            # stops, and X is carried as two BF16 terms (two MMAs per iteration)
+            ex_tf = 2 * 2.0 * na_s * na_s * nv * k_exec / (per[1] * 1e-3) / 1e12
+            tc_extra.update({"executed_iterations_per_voxel": k_exec, "tensor_tflops_executed": ex_tf,
+                             "tensor_frac_executed": ex_tf / c_peak})
     w_ach = sweep_bytes / (per[0] * 1e-3) / 1e9
     kernels = [
         {"name": "sweep", "ms": per[0], "share": per[0] / tot, "bound": "hbm",

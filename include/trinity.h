@@ -192,11 +192,14 @@ int trinity_set_initial_state(trinity_ctx* ctx, const float* I0, const float* S0
 
 /* Advance ``nsteps`` time steps.  Each step: the ray sweep (Eq. 10 with retarded upwind
  * I and S, linear in time between stored levels), the per-voxel source iteration
- * S = a P (Q + b1 S) of Eq. 12 started from S(n-1) and stopped when
- *   rho/(1-rho) |S^k - S^(k-1)|_inf <= tol * max(|S^k|_inf, 1e-6 * max|S(n-1)|)
- * (rho = a * max_d b1, a bound on the contraction) or when the change has not reached a
- * new minimum for three iterations (the iterate sits at the noise floor of the
- * arithmetic), then the detector and energy tallies.  iters_out (may be
+ * S = a P (Q + b1 S) of Eq. 12 with an isotropic rebalance after each update, started
+ * from 2 S(n-1) - S(n-2) (trinity_set_warm_start) and stopped when
+ *   rho/(1-rho) |S^k - S^(k-1)|_inf <= tol * scale,  scale = max(|S^k|_inf, 1e-6 max|S(n-1)|)
+ * (rho = a * max_d b1, a bound on the contraction) or when the iterate sits at the noise
+ * floor of the mode's arithmetic: FP32 mode, the change has not reached a new minimum for
+ * three iterations; BF16 mode, |S^k - S^(k-1)|_inf <= 2^-17 scale (the resolution of X
+ * carried as two BF16 terms) or no new minimum for two iterations.  Then the detector and
+ * energy tallies.  iters_out (may be
  * NULL) receives the largest iteration count of each step.  Returns
  * TRINITY_W_NOT_CONVERGED if any voxel hit max_iters. */
 int trinity_step(trinity_ctx* ctx, int nsteps, int* iters_out);

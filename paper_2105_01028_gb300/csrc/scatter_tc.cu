@@ -60,6 +60,7 @@ struct TcThreads {
   static constexpr int kThreads = 128 * kGroups;
 };
 constexpr int kMaxClasses = 16;
+constexpr float kResolution = 7.62939453125e-06f;  // 2^-17: relative resolution of X_hi + X_lo
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s: bound on every mbarrier wait
 
 template <int NA>
@@ -642,8 +643,10 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
           stall += 1;
         }
         const float scale = fmaxf(Sm, 1e-6f * s_glob);
-        // error bound within tol, or the change stopped shrinking (noise floor)
-        const bool conv = (rho / (1.0f - rho)) * D <= tol * scale || stall >= 3;
+        // error bound within tol, or the iterate sits at the noise floor of this mode's
+        // arithmetic: the change is below the resolution of the two-term BF16 X (2^-17 of
+        // the scale), or it stopped shrinking for two iterations
+        const bool conv = (rho / (1.0f - rho)) * D <= tol * scale || D <= kResolution * scale || stall >= 2;
         if (conv || k >= max_iters) {
           act = false;
           mine = true;
