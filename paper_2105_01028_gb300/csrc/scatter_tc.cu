@@ -503,18 +503,27 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
     }
 
     // Warm start S(n-1), or its linear extrapolation in time 2 S(n-1) - S(n-2): S_old ->
-    // TMEM, X_0 = Q + b1 S_old -> (X_hi, X_lo), and Q (read once) -> TMEM or registers.  The TMEM chunks go one at a time (not unrolled) so that
-    // their loads are not batched.
-    const auto warm = [&](int ch, float (&qc)[CH]) {
+    // TMEM, X_0 = Q + b1 S_old -> (X_hi, X_lo), and Q (read once) -> TMEM or registers.
+    // The loads of two chunks are issued together (the previous levels are not written by
+    // this kernel: read-only loads), then the two chunks are formed and stored; the TMEM
+    // chunk pairs go one pair at a time (not unrolled) so that their loads are not batched
+    // further.
+    const auto warm_load = [&](int ch, float (&s1)[CH], float (&s2)[CH], float (&qc)[CH]) {
+      const int c0 = cb + ch * CH;
+#pragma unroll
+      for (int j = 0; j < CH; ++j) {
+        const size_t col = static_cast<size_t>(c0 + j) * plane + v;
+        s1[j] = (vin && has_prev) ? __ldg(Sring + prev_base + col) : 0.0f;
+        s2[j] = (vin && has_prev2) ? __ldg(Sring + prev2_base + col) : 0.0f;
+        qc[j] = vin ? __ldg(Q + col) : 0.0f;
+      }
+    };
+    const auto warm_form = [&](int ch, const float (&s1)[CH], const float (&s2)[CH], const float (&qc)[CH]) {
       const int c0 = cb + ch * CH;
       float so[CH];
       uint32_t hi[CH / 2], lo[CH / 2];
 #pragma unroll
-      for (int j = 0; j < CH; ++j) {
-        so[j] = (vin && has_prev) ? Sring[prev_base + static_cast<size_t>(c0 + j) * plane + v] : 0.0f;
-        if (vin && has_prev2) so[j] = fmaf(2.0f, so[j], -Sring[prev2_base + static_cast<size_t>(c0 + j) * plane + v]);
-        qc[j] = vin ? __ldg(Q + static_cast<size_t>(c0 + j) * plane + v) : 0.0f;
-      }
+      for (int j = 0; j < CH; ++j) so[j] = (vin && has_prev2) ? fmaf(2.0f, s1[j], -s2[j]) : s1[j];
 #pragma unroll
       for (int j = 0; j < CH; j += 2) {
         const float b1a = kUniB1 ? sB1c[c0 + j] : b1t[sCls[c0 + j] * kM + row];
@@ -530,18 +539,28 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
             make_uint4(lo[j / 2], lo[j / 2 + 1], lo[j / 2 + 2], lo[j / 2 + 3]);
       }
     };
+    static_assert(NCT % 2 == 0, "TMEM chunks go in pairs");
 #pragma unroll 1
-    for (int ch = 0; ch < NCT; ++ch) {
-      float qc[CH];
-      warm(ch, qc);
-      tmem_st<CH>(t_q + ch * CH, qc);
+    for (int ch = 0; ch < NCT; ch += 2) {
+      float a1[CH], a2[CH], aq[CH], b1v[CH], b2v[CH], bq[CH];
+      warm_load(ch, a1, a2, aq);
+      warm_load(ch + 1, b1v, b2v, bq);
+      warm_form(ch, a1, a2, aq);
+      tmem_st<CH>(t_q + ch * CH, aq);
+      warm_form(ch + 1, b1v, b2v, bq);
+      tmem_st<CH>(t_q + (ch + 1) * CH, bq);
     }
+    {
+      constexpr int NR = NCH - NCT;  // chunks whose Q stays in registers
+      float r1[NR][CH], r2[NR][CH], rq[NR][CH];
 #pragma unroll
-    for (int ch = NCT; ch < NCH; ++ch) {
-      float qc[CH];
-      warm(ch, qc);
+      for (int u = 0; u < NR; ++u) warm_load(NCT + u, r1[u], r2[u], rq[u]);
 #pragma unroll
-      for (int j = 0; j < CH; ++j) qr[(ch - NCT) * CH + j] = qc[j];
+      for (int u = 0; u < NR; ++u) {
+        warm_form(NCT + u, r1[u], r2[u], rq[u]);
+#pragma unroll
+        for (int j = 0; j < CH; ++j) qr[u * CH + j] = rq[u][j];
+      }
     }
     tmem_wait_st();
     fence_async_smem();
@@ -699,33 +718,45 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
       const size_t pl = static_cast<size_t>(g.nv);
       float* pI = Iring + cur_base + static_cast<size_t>(cb) * pl + v;
       float* pS = Sring + cur_base + static_cast<size_t>(cb) * pl + v;
+      const float nv_v = vin ? nidx[v] : 0.0f;  // issued first: used after the stores
+      const float mu_v = vin ? mut[v] : 0.0f;
       float esum_row = 0.0f;
 #pragma unroll
-      for (int ch = 0; ch < NCH; ++ch) {
-        const int c0 = cb + ch * CH;
-        float so[CH], qv_[CH];
-        tmem_ld<CH>(t_row + C::SOFF + c0, so);
-        if (ch < NCT) tmem_ld<CH>(t_q + ch * CH, qv_);
-        tmem_wait_ld();
-        if (ch >= NCT) {
+      for (int c2 = 0; c2 < NCH; c2 += 2) {
+        float so[2][CH], qv_[2][CH];
 #pragma unroll
-          for (int j = 0; j < CH; ++j) qv_[j] = qr[(ch - NCT) * CH + j];
+        for (int u = 0; u < 2; ++u) {
+          const int ch = c2 + u;
+          if (ch >= NCH) break;
+          tmem_ld<CH>(t_row + C::SOFF + cb + ch * CH, so[u]);
+          if (ch < NCT) tmem_ld<CH>(t_q + ch * CH, qv_[u]);
         }
+        tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < CH; ++j) {
-          if (vin) {
-            const float b1 = kUniB1 ? sB1c[c0 + j] : b1t[sCls[c0 + j] * kM + row];
-            const float Iv = fmaf(b1, so[j], qv_[j]);
-            pI[static_cast<size_t>(ch * CH + j) * pl] = Iv;
-            pS[static_cast<size_t>(ch * CH + j) * pl] = so[j];
-            esum_row += Iv;
-            smax_loc = fmaxf(smax_loc, fabsf(so[j]));
+        for (int u = 0; u < 2; ++u) {
+          const int ch = c2 + u;
+          if (ch >= NCH) break;
+          const int c0 = cb + ch * CH;
+          if (ch >= NCT) {
+#pragma unroll
+            for (int j = 0; j < CH; ++j) qv_[u][j] = qr[(ch - NCT) * CH + j];
+          }
+#pragma unroll
+          for (int j = 0; j < CH; ++j) {
+            if (vin) {
+              const float b1 = kUniB1 ? sB1c[c0 + j] : b1t[sCls[c0 + j] * kM + row];
+              const float Iv = fmaf(b1, so[u][j], qv_[u][j]);
+              pI[static_cast<size_t>(ch * CH + j) * pl] = Iv;
+              pS[static_cast<size_t>(ch * CH + j) * pl] = so[u][j];
+              esum_row += Iv;
+              smax_loc = fmaxf(smax_loc, fabsf(so[u][j]));
+            }
           }
         }
       }
-      if (vin) esum += static_cast<double>(esum_row) * static_cast<double>(nidx[v]);
+      if (vin) esum += static_cast<double>(esum_row) * static_cast<double>(nv_v);
       // absorbed energy: mu_a sum_d I, one shared atomic per warp
-      float ab = vin ? esum_row * (ev * mut[v]) : 0.0f;
+      float ab = vin ? esum_row * (ev * mu_v) : 0.0f;
 #pragma unroll
       for (int o = 16; o >= 1; o >>= 1) ab += __shfl_xor_sync(0xffffffffu, ab, o);
       if (lane == 0) atomicAdd(&asum_sh, static_cast<double>(ab));
