@@ -84,6 +84,9 @@ struct trinity_ctx {
   // TMA-staged sweep (uniform n, vacuum faces, nx % 4 == 0): tensor maps of the rings and
   // the directions of each dominant-axis class
   bool tma = false;
+  // BF16 iteration: TMA descriptors of the I and S rings for the tiles' write-out
+  alignas(64) unsigned char out_maps[256] = {};
+  bool tma_out = false;
   cudaStream_t side[2] = {nullptr, nullptr};  // the TMA sweep's classes run concurrently
   cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
   SweepMaps maps{};
@@ -381,6 +384,7 @@ BfTables bf_tables(trinity_ctx* c) {
   t.cls_ds = c->d_cls_ds;
   t.ncls = c->ncls;
   t.nch = c->nch;
+  t.out_maps = c->tma_out ? c->out_maps : nullptr;
   return t;
 }
 
@@ -864,6 +868,10 @@ int trinity_create_grid(const trinity_grid_desc* desc, void* cuda_stream, trinit
   if (!ctx->two_level) {
     ctx->Qc = ctx->Q;  // one grid: the scatter reads Q and writes I directly
     ctx->Ic = ctx->I;
+  }
+  if (desc->precision == TRINITY_BF16) {
+    ctx->tma_out = make_scatter_out_maps(ctx->g_s, ctx->Ic, ctx->S, ctx->out_maps) == cudaSuccess;
+    if (!ctx->tma_out) cudaGetLastError();  // plain stores
   }
   if (g.mirror) {
     // refl[d][mask]: the direction of Omega_d with the components of the axes in mask

@@ -65,7 +65,12 @@ struct BfTables {
   const float* cls_ds;   // [ncls][nch] spacings of each class (b1 = mean of their b1)
   int ncls;              // <= 16
   int nch;               // 1, or the children per coarse direction on a two-level grid
+  // TMA descriptors of the I and S rings (4-D: x, y, z, plane; boxes of one 8 x 4 x 4
+  // brick and 8 directions) through which the tile's write-out is stored, or null: plain
+  // stores.  Built by make_scatter_out_maps (nx a multiple of 4).
+  const void* out_maps;  // 2 x 128 bytes
 };
+cudaError_t make_scatter_out_maps(const GridParams& gs, float* Iring, float* Sring, void* out);
 
 __host__ __device__ inline int ring_slot(int level) { return ((level % 5) + 5) % 5; }
 

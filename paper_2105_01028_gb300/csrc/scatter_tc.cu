@@ -40,10 +40,13 @@
 // a tile iterates until its slowest voxel stops, and the iteration count varies smoothly
 // in space, so a compact brick wastes fewer iterations than a run of 128 voxels along x.
 // A warp's 32 rows are four 8-voxel x-runs: 32-byte sectors, as coalesced as one run.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 
 #include "device.cuh"
 
@@ -317,7 +320,8 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
                       const float* __restrict__ cls_ds, int ncls, int nch, const uint16_t* __restrict__ Pbf,
                       const float* __restrict__ Q, const float* __restrict__ mut, const float* __restrict__ eps,
                       const float* __restrict__ nidx, float* __restrict__ Iring, float* __restrict__ Sring,
-                      float tol, int max_iters, RunState rs) {
+                      float tol, int max_iters, const __grid_constant__ CUtensorMap tmOutI,
+                      const __grid_constant__ CUtensorMap tmOutS, int tma_out, RunState rs) {
   using C = Tc<NA>;
   constexpr int CH = C::CH;  // TMEM load width
   constexpr int NCH = C::HALF / CH;
@@ -448,8 +452,11 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
   };
 
   while (true) {
-    // the next tile is claimed one tile ahead so that its inputs can be prefetched into L2
+    // the next tile is claimed one tile ahead so that its inputs can be prefetched into L2;
+    // the previous tile's TMA stores must have read the staging area (the X operands)
+    // before the warm start writes X again
     if (tid == 0) {
+      if (tma_out) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
       tile_s = first_tile ? atomicAdd(rs.tile_ctr + (n & 1), 1) : next_s;
       next_s = atomicAdd(rs.tile_ctr + (n & 1), 1);
     }
@@ -714,6 +721,77 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
     // Write out the tile: I = Q + b1 S and S of every voxel, from TMEM (a voxel's S stays
     // there unchanged once it has stopped).  At the tile's end, so that a warp stores whole
     // 32-byte sectors (a brick row of eight voxels) instead of pieces as its rows stop.
+    if (C::KP == NA && tma_out) {
+      // staged: I (round 0) and then S (round 1) of the whole tile go to the X operand
+      // area as 8-direction boxes of the brick ([direction][row], conflict-free) and one
+      // thread stores them with TMA; round 0's stores must have read the area before S is
+      // written there, round 1's before the next tile's warm start
+      float* stg = reinterpret_cast<float*>(sAhi);
+      const int bx = tile % bxn, t2 = tile / bxn;
+      const int ox = bx << 3, oy = (t2 % byn) << 2, oz = (t2 / byn) << 2;
+      const int pbase = ring_slot(n) * NA;
+      const float nv_v = vin ? nidx[v] : 0.0f;
+      const float mu_v = vin ? mut[v] : 0.0f;
+      float esum_row = 0.0f;
+#pragma unroll 1
+      for (int rnd = 0; rnd < 2; ++rnd) {
+#pragma unroll
+        for (int c2 = 0; c2 < NCH; c2 += 2) {
+          float so[2][CH], qv_[2][CH];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int ch = c2 + u;
+            if (ch >= NCH) break;
+            tmem_ld<CH>(t_row + C::SOFF + cb + ch * CH, so[u]);
+            if (ch < NCT && rnd == 0) tmem_ld<CH>(t_q + ch * CH, qv_[u]);
+          }
+          tmem_wait_ld();
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int ch = c2 + u;
+            if (ch >= NCH) break;
+            const int c0 = cb + ch * CH;
+            if (ch >= NCT) {
+#pragma unroll
+              for (int j = 0; j < CH; ++j) qv_[u][j] = qr[(ch - NCT) * CH + j];
+            }
+#pragma unroll
+            for (int j = 0; j < CH; ++j) {
+              const int col = c0 + j;
+              float val = so[u][j];
+              if (rnd == 0) {
+                const float b1 = kUniB1 ? sB1c[col] : b1t[sCls[col] * kM + row];
+                val = fmaf(b1, so[u][j], qv_[u][j]);
+                if (vin) {
+                  esum_row += val;
+                  smax_loc = fmaxf(smax_loc, fabsf(so[u][j]));
+                }
+              }
+              stg[(col >> 3) * 1024 + (col & 7) * 128 + row] = val;
+            }
+          }
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+          const uint64_t map = reinterpret_cast<uint64_t>(rnd == 0 ? &tmOutI : &tmOutS);
+#pragma unroll 1
+          for (int bb = 0; bb < NA / 8; ++bb)
+            asm volatile(
+                "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(map),
+                "r"(ox), "r"(oy), "r"(oz), "r"(pbase + bb * 8), "r"(smem_u32(stg + bb * 1024))
+                : "memory");
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+          if (rnd == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        }
+        if (rnd == 0) __syncthreads();
+      }
+      if (vin) esum += static_cast<double>(esum_row) * static_cast<double>(nv_v);
+      float ab = vin ? esum_row * (ev * mu_v) : 0.0f;
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) ab += __shfl_xor_sync(0xffffffffu, ab, o);
+      if (lane == 0) atomicAdd(&asum_sh, static_cast<double>(ab));
+    } else
     {
       const size_t pl = static_cast<size_t>(g.nv);
       float* pI = Iring + cur_base + static_cast<size_t>(cb) * pl + v;
@@ -783,6 +861,7 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
   }
 
   if (aborted && tid == 0) atomicExch(rs.error, 2);
+  if (tma_out && tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   // energy and max |S| of this CTA's voxels
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) {
@@ -911,26 +990,63 @@ bool scatter_bf16_supported(int na) {
   return true;
 }
 
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode_out = nullptr;
+
+cudaError_t make_scatter_out_maps(const GridParams& gs, float* Iring, float* Sring, void* out) {
+  if (gs.nx % 4 != 0 || gs.na % 8 != 0) return cudaErrorNotSupported;  // 16-byte strides, whole boxes
+  if (!g_encode_out) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    g_encode_out = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[4] = {static_cast<cuuint64_t>(gs.nx), static_cast<cuuint64_t>(gs.ny),
+                              static_cast<cuuint64_t>(gs.nz), static_cast<cuuint64_t>(5) * gs.na};
+  const cuuint64_t strides[3] = {static_cast<cuuint64_t>(gs.nx) * 4, static_cast<cuuint64_t>(gs.nx) * gs.ny * 4,
+                                 static_cast<cuuint64_t>(gs.nv) * 4};
+  const cuuint32_t box[4] = {8, 4, 4, 8};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  for (int k = 0; k < 2; ++k) {
+    const CUresult r = g_encode_out(reinterpret_cast<CUtensorMap*>(static_cast<unsigned char*>(out) + 128 * k),
+                                    CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, k == 0 ? Iring : Sring, dims, strides, box,
+                                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                    CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_scatter_bf16(const GridParams& g, const BfTables& t, const uint16_t* Pbf, const float* Q,
                                 const float* mut, const float* eps, const float* nidx, float* Iring,
                                 float* Sring, float tol, int max_iters, RunState rs, cudaStream_t st) {
+  CUtensorMap mI, mS;
+  std::memset(&mI, 0, sizeof(mI));
+  std::memset(&mS, 0, sizeof(mS));
+  // the staging area is the X operands: only where they carry no zero K padding (the
+  // padding must stay zero, and 192 directions fill K exactly)
+  const int tma_out = (t.out_maps && g.na % 64 == 0) ? 1 : 0;
+  if (tma_out) {
+    std::memcpy(&mI, t.out_maps, sizeof(CUtensorMap));
+    std::memcpy(&mS, static_cast<const unsigned char*>(t.out_maps) + 128, sizeof(CUtensorMap));
+  }
   const int ntiles = brick_tiles(g.nx, g.ny, g.nz);
   const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
   const bool uni = g.mut_u >= 0.0f;
   if (g.na == 48) {
     if (uni)
       scatter_tc_kernel<48, true><<<grid, Tc<48>::kThreads, Tc<48>::SMEM, st>>>(
-          g, t.rcorr, t.cls, t.cls_ds, t.ncls, t.nch, Pbf, Q, mut, eps, nidx, Iring, Sring, tol, max_iters, rs);
+          g, t.rcorr, t.cls, t.cls_ds, t.ncls, t.nch, Pbf, Q, mut, eps, nidx, Iring, Sring, tol, max_iters, mI, mS, tma_out, rs);
     else
       scatter_tc_kernel<48, false><<<grid, Tc<48>::kThreads, Tc<48>::SMEM, st>>>(
-          g, t.rcorr, t.cls, t.cls_ds, t.ncls, t.nch, Pbf, Q, mut, eps, nidx, Iring, Sring, tol, max_iters, rs);
+          g, t.rcorr, t.cls, t.cls_ds, t.ncls, t.nch, Pbf, Q, mut, eps, nidx, Iring, Sring, tol, max_iters, mI, mS, tma_out, rs);
   } else if (g.na == 192) {
     if (uni)
       scatter_tc_kernel<192, true><<<grid, Tc<192>::kThreads, Tc<192>::SMEM, st>>>(
-          g, t.rcorr, t.cls, t.cls_ds, t.ncls, t.nch, Pbf, Q, mut, eps, nidx, Iring, Sring, tol, max_iters, rs);
+          g, t.rcorr, t.cls, t.cls_ds, t.ncls, t.nch, Pbf, Q, mut, eps, nidx, Iring, Sring, tol, max_iters, mI, mS, tma_out, rs);
     else
       scatter_tc_kernel<192, false><<<grid, Tc<192>::kThreads, Tc<192>::SMEM, st>>>(
-          g, t.rcorr, t.cls, t.cls_ds, t.ncls, t.nch, Pbf, Q, mut, eps, nidx, Iring, Sring, tol, max_iters, rs);
+          g, t.rcorr, t.cls, t.cls_ds, t.ncls, t.nch, Pbf, Q, mut, eps, nidx, Iring, Sring, tol, max_iters, mI, mS, tma_out, rs);
   } else {
     return cudaErrorInvalidValue;
   }
