@@ -432,29 +432,11 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
   float qr[C::QR > 0 ? C::QR : 1];  // Q of the thread's last QR columns
   bool first_tile = true;
 
-  // L2 prefetch of a tile's inputs (Q and the start levels of S, and the rows' optics):
-  // lane l of a warp takes 8-voxel run l % 4 of the warp's 32 rows (one 32-byte sector
-  // per column) and every eighth of the thread's column group starting at l / 4.
-  const auto prefetch_tile = [&](int t) {
-    if (t >= ntiles) return;
-    const int vr = brick_voxel(g, bxn, byn, t, ((warp & 3) << 5) + ((lane & 3) << 3));
-    if (vr < 0) return;
-    if (half == 0 && lane < 4) {
-      asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(eps + vr));
-      asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(mut + vr));
-    }
-    for (int j = lane >> 2; j < C::HALF; j += 8) {
-      const size_t col = static_cast<size_t>(cb + j) * plane + vr;
-      asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(Q + col));
-      if (has_prev) asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(Sring + prev_base + col));
-      if (has_prev2) asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(Sring + prev2_base + col));
-    }
-  };
 
   while (true) {
-    // the next tile is claimed one tile ahead so that its inputs can be prefetched into L2;
-    // the previous tile's TMA stores must have read the staging area (the X operands)
-    // before the warm start writes X again
+    // the next tile is claimed when this one starts (its atomic is off the next tile's
+    // path); the previous tile's TMA stores must have read the staging area (the X
+    // operands) before the warm start writes X again
     if (tid == 0) {
       if (tma_out) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
       tile_s = first_tile ? atomicAdd(rs.tile_ctr + (n & 1), 1) : next_s;
@@ -463,7 +445,6 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
     first_tile = false;
     __syncthreads();
     const int tile = tile_s;
-    const int next_tile = next_s;
     if (tile >= ntiles) break;
     const int vb = brick_voxel(g, bxn, byn, tile, row);
     const bool vin = vb >= 0;
@@ -717,7 +698,6 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
       }
     }
     if (aborted) break;
-    prefetch_tile(next_tile);  // lands while this tile is written out
     // Write out the tile: I = Q + b1 S and S of every voxel, from TMEM (a voxel's S stays
     // there unchanged once it has stopped).  At the tile's end, so that a warp stores whole
     // 32-byte sectors (a brick row of eight voxels) instead of pieces as its rows stop.
