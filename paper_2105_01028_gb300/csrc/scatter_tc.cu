@@ -702,10 +702,10 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
     // there unchanged once it has stopped).  At the tile's end, so that a warp stores whole
     // 32-byte sectors (a brick row of eight voxels) instead of pieces as its rows stop.
     if (C::KP == NA && tma_out) {
-      // staged: I (round 0) and then S (round 1) of the whole tile go to the X operand
-      // area as 8-direction boxes of the brick ([direction][row], conflict-free) and one
-      // thread stores them with TMA; round 0's stores must have read the area before S is
-      // written there, round 1's before the next tile's warm start
+      // staged: I (first pass) and then S (second pass) of the whole tile go to the X
+      // operand area as 8-direction boxes of the brick ([direction][row], conflict-free)
+      // and one thread stores them with TMA; the first pass's stores must have read the
+      // area before S is written there, the second pass's before the next tile's warm start
       float* stg = reinterpret_cast<float*>(sAhi);
       const int bx = tile % bxn, t2 = tile / bxn;
       const int ox = bx << 3, oy = (t2 % byn) << 2, oz = (t2 / byn) << 2;
@@ -714,7 +714,7 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
       const float mu_v = vin ? mut[v] : 0.0f;
       float esum_row = 0.0f;
 #pragma unroll 1
-      for (int rnd = 0; rnd < 2; ++rnd) {
+      for (int pass = 0; pass < 2; ++pass) {
 #pragma unroll
         for (int c2 = 0; c2 < NCH; c2 += 2) {
           float so[2][CH], qv_[2][CH];
@@ -723,7 +723,7 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
             const int ch = c2 + u;
             if (ch >= NCH) break;
             tmem_ld<CH>(t_row + C::SOFF + cb + ch * CH, so[u]);
-            if (ch < NCT && rnd == 0) tmem_ld<CH>(t_q + ch * CH, qv_[u]);
+            if (ch < NCT && pass == 0) tmem_ld<CH>(t_q + ch * CH, qv_[u]);
           }
           tmem_wait_ld();
 #pragma unroll
@@ -739,7 +739,7 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
             for (int j = 0; j < CH; ++j) {
               const int col = c0 + j;
               float val = so[u][j];
-              if (rnd == 0) {
+              if (pass == 0) {
                 const float b1 = kUniB1 ? sB1c[col] : b1t[sCls[col] * kM + row];
                 val = fmaf(b1, so[u][j], qv_[u][j]);
                 if (vin) {
@@ -754,7 +754,7 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
         fence_async_smem();
         __syncthreads();
         if (tid == 0) {
-          const uint64_t map = reinterpret_cast<uint64_t>(rnd == 0 ? &tmOutI : &tmOutS);
+          const uint64_t map = reinterpret_cast<uint64_t>(pass == 0 ? &tmOutI : &tmOutS);
 #pragma unroll 1
           for (int bb = 0; bb < NA / 8; ++bb)
             asm volatile(
@@ -762,9 +762,9 @@ __global__ void __launch_bounds__(TcThreads<NA>::kThreads, 1)
                 "r"(ox), "r"(oy), "r"(oz), "r"(pbase + bb * 8), "r"(smem_u32(stg + bb * 1024))
                 : "memory");
           asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-          if (rnd == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+          if (pass == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
         }
-        if (rnd == 0) __syncthreads();
+        if (pass == 0) __syncthreads();
       }
       if (vin) esum += static_cast<double>(esum_row) * static_cast<double>(nv_v);
       float ab = vin ? esum_row * (ev * mu_v) : 0.0f;
