@@ -94,8 +94,11 @@ def test_bf16_small_config_fields_and_energy(small_pair):
     assert _rel_l2(out["N"], np.array(ref.energy)) <= BF16_TOL
 
 
-@pytest.mark.parametrize("shape,nside,steps", [((13, 11, 9), 2, 30), ((9, 7, 12), 4, 24)])
+@pytest.mark.parametrize("shape,nside,steps", [((13, 11, 9), 2, 30), ((9, 7, 12), 4, 24), ((20, 10, 6), 4, 24)])
 def test_bf16_ragged_grids(shape, nside, steps):
+    """Grids that leave partial 8 x 4 x 4 voxel bricks; at 192 directions with nx a multiple
+    of 4 (20 x 10 x 6) the tiles are written out through TMA tensor stores, which clip the
+    partial bricks at the grid's edges."""
     T = _gpu()
     nx, ny, nz = shape
     prob = W.homogeneous(nx, ny, nz, nside, 0.02, 3.0, steps=steps, precision="bf16")
