@@ -402,24 +402,36 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t t = tmem + (static_cast<uint32_t>(q4 * 32) << 16) + buf * 256u + static_cast<uint32_t>(c0);
       const float* b1c = b1s + it.cls * kNa + c0;
       float erow = 0.0f;
+      // two 16-column chunks at a time: their 32 Q loads are issued before the TMEM loads
+      static_assert((kEpiCols / kEpiCh) % 2 == 0, "chunks go in pairs");
 #pragma unroll 1
-      for (int ch = 0; ch < kEpiCols / kEpiCh; ++ch) {
-        float sv[kEpiCh];
-        tmem_ld16(t + ch * kEpiCh, sv);
+      for (int ch = 0; ch < kEpiCols / kEpiCh; ch += 2) {
+        float qv[2][kEpiCh];
         if (mine) {
-          const float* qp = Q + static_cast<size_t>(c0 + ch * kEpiCh) * plane + v;
-          float qv[kEpiCh];
 #pragma unroll
-          for (int j = 0; j < kEpiCh; ++j) qv[j] = __ldcs(qp + static_cast<size_t>(j) * plane);
-          float* ip = Iring + cur + static_cast<size_t>(c0 + ch * kEpiCh) * plane + v;
-          float* sp = Sring + cur + static_cast<size_t>(c0 + ch * kEpiCh) * plane + v;
+          for (int u = 0; u < 2; ++u) {
+            const float* qp = Q + static_cast<size_t>(c0 + (ch + u) * kEpiCh) * plane + v;
 #pragma unroll
-          for (int j = 0; j < kEpiCh; ++j) {
-            const float Iv = fmaf(b1c[ch * kEpiCh + j], sv[j], qv[j]);
-            __stcs(ip + static_cast<size_t>(j) * plane, Iv);
-            __stcs(sp + static_cast<size_t>(j) * plane, sv[j]);
-            erow += Iv;
-            smax = fmaxf(smax, fabsf(sv[j]));
+            for (int j = 0; j < kEpiCh; ++j) qv[u][j] = __ldcs(qp + static_cast<size_t>(j) * plane);
+          }
+        }
+        float sv[2][kEpiCh];
+        tmem_ld16(t + ch * kEpiCh, sv[0]);
+        tmem_ld16(t + (ch + 1) * kEpiCh, sv[1]);
+        if (mine) {
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int cc = (ch + u) * kEpiCh;
+            float* ip = Iring + cur + static_cast<size_t>(c0 + cc) * plane + v;
+            float* sp = Sring + cur + static_cast<size_t>(c0 + cc) * plane + v;
+#pragma unroll
+            for (int j = 0; j < kEpiCh; ++j) {
+              const float Iv = fmaf(b1c[cc + j], sv[u][j], qv[u][j]);
+              __stcs(ip + static_cast<size_t>(j) * plane, Iv);
+              __stcs(sp + static_cast<size_t>(j) * plane, sv[u][j]);
+              erow += Iv;
+              smax = fmaxf(smax, fabsf(sv[u][j]));
+            }
           }
         }
       }
