@@ -261,9 +261,14 @@ int trinity_steps_done(const trinity_ctx* ctx, int* n);
 int trinity_kernels_per_step(const trinity_ctx* ctx, int* n);
 
 /* Form of the ray sweep a step runs: 0 plain loads (one kernel), 1 upwind planes staged
- * through TMA tile loads (one kernel per dominant-axis class: vacuum faces, a uniform
- * refractive index, nx a multiple of 4), 2 the fused two-level sweep. */
+ * through TMA tile loads (one kernel per dominant-axis class, run concurrently: vacuum
+ * faces, a uniform refractive index, nx a multiple of 4), 2 the fused two-level sweep. */
 int trinity_sweep_form(const trinity_ctx* ctx, int* form);
+
+/* on = 0: the plain-load sweep even where the TMA-staged one applies (both perform the
+ * same FP32 operations on the same values, so results are bit-identical); on = 1
+ * (default): the TMA-staged sweep where it applies.  Before the first step. */
+int trinity_set_sweep_tma(trinity_ctx* ctx, int on);
 
 /* Zero the fields, tallies and step counter; keep grid, optics, source and detectors. */
 int trinity_reset(trinity_ctx* ctx);

@@ -82,6 +82,8 @@ class Forward:
         self._check(self.set_optics(prob["mua"], prob["mus"], prob["nidx"], prob["g"]))
         if prob.get("fresnel", False):
             self._check(self.L.trinity_set_fresnel(self.h, 1))
+        if not prob.get("sweep_tma", True):  # the plain-load sweep (bit-identical results)
+            self._check(self.L.trinity_set_sweep_tma(self.h, 0))
         warm = prob.get("warm_start", "extrapolated")  # or "previous": S(n-1) as the paper states
         if warm not in ("extrapolated", "previous"):
             raise ValueError("warm_start must be 'extrapolated' or 'previous'")

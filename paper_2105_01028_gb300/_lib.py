@@ -70,6 +70,7 @@ SIGNATURES = {
     "trinity_read_energy": (c_int, [c_void_p, P_double, P_double, P_double, P_double, c_size_t]),
     "trinity_kernels_per_step": (c_int, [c_void_p, P_int]),
     "trinity_sweep_form": (c_int, [c_void_p, P_int]),
+    "trinity_set_sweep_tma": (c_int, [c_void_p, c_int]),
     "trinity_read_iterations": (c_int, [c_void_p, P_int, P_double, c_size_t]),
     "trinity_read_executed_iterations": (c_int, [c_void_p, P_double, c_size_t]),
     "trinity_read_field": (c_int, [c_void_p, c_int, c_int, c_void_p, c_size_t, c_int]),

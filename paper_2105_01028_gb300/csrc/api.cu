@@ -88,6 +88,7 @@ struct trinity_ctx {
   alignas(64) unsigned char out_maps[256] = {};
   bool tma_out = false;
   cudaStream_t side[2] = {nullptr, nullptr};  // the TMA sweep's classes run concurrently
+  bool tma_off = false;                       // trinity_set_sweep_tma(ctx, 0)
   cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
   SweepMaps maps{};
   int* d_dlist[3] = {nullptr, nullptr, nullptr};
@@ -531,12 +532,18 @@ int restore_checkpoint(trinity_ctx* ctx, int k, int c, bool store) {
 
 // Sweep (Eq. 10's known part Q) and the interface split; on a two-level grid also the
 // mean of Q over each coarse direction's children.
+// The step's sweep stages its upwind planes through the TMA: supported box, uniform
+// refractive index (one retarded delay per direction), not switched off.
+bool sweep_uses_tma(const trinity_ctx* ctx) {
+  return !ctx->two_level && ctx->tma && !ctx->tma_off && ctx->g.n_u >= 1.0f;
+}
+
 int enqueue_transport(trinity_ctx* ctx, const RunState& rs) {
   const GridParams& g = ctx->g;
   if (ctx->two_level) {
     CK(launch_sweep2(g, ctx->d_dirs, ctx->d_offs, ctx->d_children, ctx->nch, ctx->na_s, ctx->I, ctx->S,
                      ctx->mut, ctx->nidx, ctx->Q, ctx->Qc, rs, ctx->stream));
-  } else if (ctx->tma && g.n_u >= 1.0f) {
+  } else if (sweep_uses_tma(ctx)) {
     const int* dl[3] = {ctx->d_dlist[0], ctx->d_dlist[1], ctx->d_dlist[2]};
     // the three dominant-axis classes on the context's stream and two side streams (forked
     // and joined by events, so a captured step holds them as parallel graph nodes)
@@ -1044,6 +1051,7 @@ int trinity_set_optics(trinity_ctx* ctx, const float* mua, const float* mus, con
   ctx->g_s.mut_u = ctx->g.mut_u;
   ctx->g_s.n_u = ctx->g.n_u;
   ctx->nmap = r;
+
   ctx->h_P32 = P32;
   ctx->h_rc32 = rc;
   ctx->h_mut = mt;
@@ -1717,7 +1725,7 @@ int trinity_kernels_per_step(const trinity_ctx* ctx, int* n) {
   int k = 0;
   if (ctx->two_level)
     k = 1 + 1 + 1 + 1;  // sweep2, scatter, refine, tally
-  else if (ctx->tma && ctx->g.n_u >= 1.0f)
+  else if (sweep_uses_tma(ctx))
     k = (ctx->ndir[0] > 0) + (ctx->ndir[1] > 0) + (ctx->ndir[2] > 0) + 1 + 1;  // sweeps, scatter, tally
   else
     k = 1 + 1 + 1;  // sweep, scatter, tally
@@ -1728,7 +1736,14 @@ int trinity_kernels_per_step(const trinity_ctx* ctx, int* n) {
 
 int trinity_sweep_form(const trinity_ctx* ctx, int* form) {
   if (!ctx || !form) return TRINITY_E_INVALID;
-  *form = ctx->two_level ? 2 : ((ctx->tma && ctx->g.n_u >= 1.0f) ? 1 : 0);
+  *form = ctx->two_level ? 2 : (sweep_uses_tma(ctx) ? 1 : 0);
+  return TRINITY_OK;
+}
+
+int trinity_set_sweep_tma(trinity_ctx* ctx, int on) {
+  if (!ctx) return TRINITY_E_INVALID;
+  if (ctx->locked) return fail(ctx, TRINITY_E_STATE, "the sweep form must be chosen before the first step");
+  ctx->tma_off = on == 0;
   return TRINITY_OK;
 }
 

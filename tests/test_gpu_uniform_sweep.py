@@ -68,11 +68,11 @@ def test_uniform_forms_match_per_voxel_forms(precision, nside_scatter):
                                        (1, (44, 10, 9)), (5, (44, 10, 9))])
 def test_tma_sweep_matches_plain_sweep(face, grid):
     """With a uniform refractive index, vacuum faces and nx a multiple of 4 the sweep stages
-    its upwind planes through the TMA (one kernel per dominant-axis class); changing n in
-    one unreachable corner voxel sends the step through the plain-load sweep.  The pulse
-    enters through an x, y or z face so that each class sees the source face's inflow;
-    nx = 44 gives the x-dominant items a full 32-voxel chunk and a ragged one.  Fields must
-    agree bit for bit."""
+    its upwind planes through the TMA (one kernel per dominant-axis class).  Against the
+    plain-load sweep of the same description, and with n changed in one unreachable corner
+    voxel (which sends the step through the plain sweep's per-voxel delays), fields must
+    agree bit for bit.  The pulse enters through an x, y or z face so that each class sees the source
+    face's inflow; nx = 44 gives the x-dominant items a full 32-voxel chunk and a ragged one."""
     P = _lib()
     n = grid
     p = W.homogeneous(n[0], n[1], n[2], 4, 0.01, 2.0, steps=STEPS, tol=1e-6)
@@ -87,6 +87,13 @@ def test_tma_sweep_matches_plain_sweep(face, grid):
     assert launches == 6 and form == "tma"  # three sweep classes, scatter, tallies, step counter
     base = _run(p)
     assert np.max(np.abs(base["I"])) > 0
+    plain = dict(p, sweep_tma=False)
+    fw = P.Forward(plain)
+    assert fw.kernels_per_step() == 4 and fw.sweep_form() == "plain"
+    fw.close()
+    got = _run(plain)
+    for k in ("I", "S", "I1"):
+        assert np.array_equal(got[k], base[k]), k
     q = dict(p)
     q["nidx"] = p["nidx"].copy()
     q["nidx"][-1, -1, -1 if face % 2 == 0 else 0] = 1.3
