@@ -570,12 +570,19 @@ def measure_window(T, torch, prob, stream, spinup, warmup, steps, what):
     executed = fwd.executed_iterations()[first:first + steps]
     kps = fwd.kernels_per_step()
     xform = fwd.exact_form()
+    sform = fwd.sweep_form()
     fwd.close()
     nv = prob["nx"] * prob["ny"] * prob["nz"]
     na = 12 * prob["nside"] ** 2
     prec = prob.get("precision", "fp32")
     kernels, roof = kernel_roofline(nv, na, na, kms, kp, float(np.mean(k_it_mean[-kp:])), prec, peaks(),
                                     exact=xform)
+    # measured DRAM bytes of the dominant kernel (committed ncu table, while its source is unchanged)
+    names = {"sweep": {"tma": "sweep_tma_kernel", "plain": "sweep_kernel"}.get(sform, "sweep2_kernel"),
+             "exact_tc": "exact_tc_kernel", "exact_fp32": "exact_gemm192_kernel",
+             "scatter_bf16": "scatter_tc_kernel", "scatter_fp32": "scatter_fp32_kernel"}
+    if roof["kernel"] in names:
+        roof["traffic"] = measured_traffic(names[roof["kernel"]], nv * na)
     return {"workload": what, "precision": prec, "value": nv * na * steps / (ms * 1e-3), "unit": "updates/s",
             "ms_per_step": ms / steps, "window": "time steps %d..%d" % (first, first + steps - 1),
             "iterations": {"mean": float(np.mean(it_mean[first:first + steps])),
