@@ -544,7 +544,7 @@ def kernel_roofline(nv, na, na_s, kms, kp, k_mean, precision, pk, exact=None):
     return kernels, roof
 
 
-def measure_window(T, torch, prob, stream, spinup, warmup, steps, what):
+def measure_window(T, torch, prob, stream, spinup, warmup, steps, what, slab_traffic=True):
     """One more workload for the bench line: spin the solve up for ``spinup`` steps, run
     ``warmup`` more, then time ``steps`` graph-replayed steps with CUDA events on the
     library's stream (clocks sampled meanwhile), and time up to 10 further steps kernel
@@ -577,11 +577,12 @@ def measure_window(T, torch, prob, stream, spinup, warmup, steps, what):
     prec = prob.get("precision", "fp32")
     kernels, roof = kernel_roofline(nv, na, na, kms, kp, float(np.mean(k_it_mean[-kp:])), prec, peaks(),
                                     exact=xform)
-    # measured DRAM bytes of the dominant kernel (committed ncu table, while its source is unchanged)
+    # measured DRAM bytes of the dominant kernel (committed ncu table, captured on the slab,
+    # while its source is unchanged); not for workloads whose kernel instances differ
     names = {"sweep": {"tma": "sweep_tma_kernel", "plain": "sweep_kernel"}.get(sform, "sweep2_kernel"),
              "exact_tc": "exact_tc_kernel", "exact_fp32": "exact_gemm192_kernel",
              "scatter_bf16": "scatter_tc_kernel", "scatter_fp32": "scatter_fp32_kernel"}
-    if roof["kernel"] in names:
+    if slab_traffic and roof["kernel"] in names:
         roof["traffic"] = measured_traffic(names[roof["kernel"]], nv * na)
     return {"workload": what, "precision": prec, "value": nv * na * steps / (ms * 1e-3), "unit": "updates/s",
             "ms_per_step": ms / steps, "window": "time steps %d..%d" % (first, first + steps - 1),
@@ -864,7 +865,8 @@ def main():
             T, torch, p3, stream, args.spinup, args.warmup, args.steps,
             "heterogeneous phantom 128x128x96 @1mm, 192 dirs, slab optics, air cylinder r 5 mm (n 1) with "
             "Fresnel refraction/reflection at its wall, 3 absorbing spheres r 4/6/8 mm (mu_a x2/x3.5/x5), "
-            "-x face pulse, 8 detectors; BF16 scatter, FP32 sweep, general per-voxel kernel forms")
+            "-x face pulse, 8 detectors; BF16 scatter, FP32 sweep, general per-voxel kernel forms",
+            slab_traffic=False)
         pe = W.config_slab(steps=total, precision="fp32", nx=nx, ny=ny, nz=nz)
         pe["exact"] = True
         line["exact"] = measure_window(
